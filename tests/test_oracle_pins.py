@@ -1,0 +1,306 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks a closed form, an
+invariant the method guarantees, a special case that reduces to textbook SPH,
+brute force, quadrature, finite differences, or a number the paper prints
+(tests/golden/paper_constants.json).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from paper_2511_21921_gb300 import synth
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+
+
+def _params(**kw):
+    return oracle.default_params(**kw)
+
+
+# ---------------------------------------------------------------- kernel
+def test_wendland_normalised_by_quadrature():
+    """Wendland C4 with support h integrates to one over the ball (Sec. 2.1)."""
+    for h in (0.05, 0.3, 1.0):
+        f = lambda r: 4 * np.pi * r * r * oracle.kernel(np.array([r]), h)[0][0]
+        val, err = integrate.quad(f, 0.0, h, epsabs=1e-14, epsrel=1e-13, limit=200)
+        assert abs(val - 1.0) < 1e-12, (h, val)
+    # compact support of radius h, not 2h (App. A.2 footnote)
+    W, dW, g = oracle.kernel(np.array([1.0, 1.2, 2.0]) * 0.3, 0.3)
+    assert GOLD["kernel_radius_is_h"]["value"]
+    assert np.all(W == 0) and np.all(dW == 0) and np.all(g == 0)
+
+
+def test_wendland_derivative_by_finite_differences():
+    h = 0.2
+    r = np.linspace(0.003, 0.197, 97)
+    eps = 1e-6
+    Wp = oracle.kernel(r + eps, h)[0]
+    Wm = oracle.kernel(r - eps, h)[0]
+    fd = (Wp - Wm) / (2 * eps)
+    W, dW, g = oracle.kernel(r, h)
+    assert np.allclose(dW, fd, rtol=1e-7, atol=1e-7 * np.abs(fd).max())
+    assert np.allclose(g * r, dW, rtol=1e-13, atol=0)
+    # smooth at the origin: g(0) is finite and W'(0) = 0
+    W0, dW0, g0 = oracle.kernel(np.array([0.0]), h)
+    assert dW0[0] == 0 and np.isfinite(g0[0]) and g0[0] < 0
+
+
+# ---------------------------------------------------------------- neighbors
+def _brute(x, h, L, mode):
+    n = h.shape[0]
+    d = x[:, :, None] - x[:, None, :]
+    d = np.where(d > L / 2, d - L, np.where(d < -L / 2, d + L, d))
+    r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2]
+    if mode == "gather":
+        M = r2 < (h * h)[:, None]
+    else:
+        M = (r2 < (h * h)[:, None]) | (r2 < (h * h)[None, :])
+        np.fill_diagonal(M, False)
+    return M
+
+
+@pytest.mark.parametrize("mode", ["gather", "union"])
+@pytest.mark.parametrize("case", ["lattice", "multiscale"])
+def test_neighbor_sets_tree_equals_brute_force(mode, case):
+    rng = np.random.default_rng(11)
+    if case == "lattice":
+        d = synth.lattice(12, seed=5)
+        x, h = d["x"], d["h"]
+    else:
+        n = 3000
+        x = rng.random((3, n))
+        h = np.exp(rng.uniform(np.log(0.01), np.log(0.25), n))
+    L = 1.0
+    row, col = oracle.neighbors(x, h, L, mode=mode, method="tree")
+    rowb, colb = oracle.neighbors(x, h, L, mode=mode, method="brute")
+    assert np.array_equal(row, rowb) and np.array_equal(col, colb)
+    M = _brute(x, h, L, mode)
+    assert np.array_equal(np.diff(row), M.sum(1))
+    for i in range(0, h.shape[0], 97):
+        assert np.array_equal(col[row[i]:row[i + 1]], np.nonzero(M[i])[0])
+
+
+def test_knn_smoothing_lengths_give_exact_neighbor_counts(lognormal32):
+    """The generator's h_i encloses exactly k_i in [90, 110] others (strict r < h)."""
+    d = lognormal32
+    o = oracle.forward(d["x"], d["h"], d["m"], L=d["L"], want=("kgather",))
+    k = o["kgather"]
+    assert k.min() >= 90 and k.max() <= 110
+
+
+# ---------------------------------------------------------------- RK pins
+def test_reproducing_conditions_and_gradient_reproduction(lognormal32):
+    """sum V W^R = 1, sum V W^R x = 0, sum V grad W^R = 0, sum V x (x) grad W^R = -I.
+
+    These fix A, B (Eq. RK) and, through the gradient identities, every term of
+    the moment gradients and of grad A, grad B.
+    """
+    d = lognormal32
+    o = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], want=("diag",))
+    dg = o["diag"]
+    assert np.abs(dg[0] - 1).max() < 1e-12
+    hs = d["h"]
+    assert np.abs(dg[1:4] / hs).max() < 1e-12
+    assert np.abs(dg[4:7] * hs).max() < 1e-10
+    assert np.abs(dg[7:16] + np.eye(3).reshape(9, 1)).max() < 1e-11
+
+
+def test_linear_velocity_gradient_exact(lognormal32):
+    """Eq. gradv reproduces a linear field exactly: v = C x + d gives grad v = C."""
+    d = lognormal32
+    x, h = d["x"], d["h"]
+    rng = np.random.default_rng(3)
+    Cm = rng.normal(size=(3, 3))
+    v = Cm @ x + rng.normal(size=(3, 1))
+    o = oracle.forward(x, h, d["m"], v, d["u"], d["L"], want=("gradv",))
+    inner = np.all((x > h) & (x < d["L"] - h), axis=0)
+    assert inner.sum() > 1000
+    gv = o["gradv"][:, inner]
+    err = np.abs(gv - Cm.reshape(9, 1)).max()
+    assert err < 1e-10, err
+
+
+def test_perfect_lattice_symmetries():
+    """On a periodic cubic lattice: equal V, B = 0, A = 1/m0, rho = m/V, and a
+    uniform pressure at rest gives no acceleration and no heating."""
+    n = 12
+    g = np.stack(np.meshgrid(*(np.arange(n),) * 3, indexing="ij")).reshape(3, -1)
+    x = (g + 0.5) / n
+    N = n ** 3
+    h = np.full(N, (3 * 64 / (4 * np.pi * N)) ** (1 / 3))
+    m = np.full(N, 1.0 / N)
+    o = oracle.forward(x, h, m, np.zeros((3, N)), np.ones(N), 1.0,
+                       want=("V", "coef", "mom", "rho", "dvdt", "dudt"))
+    V = o["V"]
+    assert np.abs(V / V.mean() - 1).max() < 1e-13
+    assert np.abs(o["coef"][1:4]).max() * h[0] < 1e-13
+    assert np.abs(o["coef"][0] * o["mom"][0] - 1).max() < 1e-13
+    assert np.abs(o["rho"] * V / m - 1).max() < 1e-13
+    scale = (GOLD["gamma"]["value"] - 1) * o["rho"].mean() * V.mean() ** 2 * 64 / h[0] ** 4 / m[0]
+    assert np.abs(o["dvdt"]).max() < 1e-12 * scale
+    assert np.abs(o["dudt"]).max() == 0.0
+
+
+def test_eos_uses_paper_gamma(lattice16):
+    d = lattice16
+    o = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], want=("rho", "P", "cs"))
+    gam = GOLD["gamma"]["value"]
+    assert np.allclose(o["P"] / (o["rho"] * d["u"]), gam - 1, rtol=1e-14)
+    assert np.allclose(o["cs"] ** 2 / d["u"], gam * (gam - 1), rtol=1e-14)
+
+
+# ---------------------------------------------------------------- rates
+def _conservation(d, o):
+    m, v, a, du = d["m"], d["v"], o["dvdt"], o["dudt"]
+    p = (m * a).sum(1)
+    e = (m * (v * a).sum(0)).sum() + (m * du).sum()
+    ps = np.abs(m * a).sum()
+    es = np.abs(m * (v * a).sum(0)).sum() + np.abs(m * du).sum()
+    return np.abs(p).max() / ps, abs(e) / es
+
+
+@pytest.mark.parametrize("relax_dt", [0.0, "partial"])
+def test_momentum_and_energy_conserved(lognormal32, relax_dt):
+    """Pairwise antisymmetric forces and the compatible energy split conserve
+    total momentum and energy to roundoff (Sec. 2.1), also with relaxation
+    applied symmetrically to some pairs (App. A.1)."""
+    d = lognormal32
+    p = _params()
+    if relax_dt == "partial":
+        o0 = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], want=("gradv",))
+        div = np.abs(o0["gradv"][0] + o0["gradv"][4] + o0["gradv"][8])
+        dt = np.log(GOLD["relax_volume_factor"]["value"]) / np.quantile(div, 0.9)
+        p = _params(relax_dt=dt)
+    o = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], params=p)
+    if relax_dt == "partial":
+        assert 0.05 < o["flag"].mean() < 0.15
+    pm, en = _conservation(d, o)
+    assert pm < 1e-13 and en < 1e-13, (pm, en)
+
+
+def test_relaxation_flag_threshold(lognormal32):
+    """Flag iff exp(|tr grad v| dt) > 8 (App. A.1)."""
+    d = lognormal32
+    o0 = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], want=("gradv",))
+    div = np.abs(o0["gradv"][0] + o0["gradv"][4] + o0["gradv"][8])
+    dt = np.log(8.0) / np.quantile(div, 0.5)
+    o = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], params=_params(relax_dt=dt),
+                       want=("flag",))
+    expect = np.exp(div * dt) > GOLD["relax_volume_factor"]["value"]
+    assert np.array_equal(o["flag"].astype(bool), expect)
+
+
+def test_fully_relaxed_inviscid_reduces_to_standard_sph(lattice16):
+    """All pairs relaxed (A=1, B=0), no viscosity, equal h: the rates are the
+    textbook SPH pressure force and compatible pdV heating, written here
+    independently by brute force."""
+    d = lattice16
+    x, h, m, v, u, L = d["x"], d["h"], d["m"], d["v"], d["u"], d["L"]
+    p = _params(Cl=0.0, Cq=0.0, relax_dt=1e9)
+    o = oracle.forward(x, h, m, v, u, L, params=p, want=("V", "P", "flag", "dvdt", "dudt"))
+    assert o["flag"].all()
+    n = h.shape[0]
+    dx = x[:, :, None] - x[:, None, :]
+    dx = np.where(dx > L / 2, dx - L, np.where(dx < -L / 2, dx + L, dx))
+    r = np.sqrt((dx ** 2).sum(0))
+    hh = h[0]
+    q = r / hh
+    # textbook Wendland C4 derivative (1/r) dW/dr, support hh
+    gr = np.where(q < 1, 495 / (32 * np.pi * hh ** 5) * (-56 / 3) * (1 - q) ** 5 * (1 + 5 * q), 0.0)
+    np.fill_diagonal(gr, 0.0)
+    V, P = o["V"], o["P"]
+    coef = V[:, None] * V[None, :] * (P[:, None] + P[None, :]) * gr  # (i, j)
+    a = -(coef[None] * dx).sum(2) / m
+    vij = v[:, :, None] - v[:, None, :]
+    du = 0.5 * (coef * (dx * vij).sum(0)).sum(1) / m
+    assert np.allclose(o["dvdt"], a, rtol=1e-10, atol=1e-12 * np.abs(a).max())
+    assert np.allclose(o["dudt"], du, rtol=1e-10, atol=1e-12 * np.abs(du).max())
+
+
+def test_viscosity_vanishes_in_pure_expansion(lognormal32):
+    """Homologous expansion v = alpha (x - c), alpha > 0: every mu >= 0, so the
+    limited viscosity adds nothing; compression with the limiter off does."""
+    d = lognormal32
+    x, h, L = d["x"], d["h"], d["L"]
+    v = 0.7 * (x - 0.5)
+    inner = np.nonzero(np.all((x > 2.5 * h.max()) & (x < L - 2.5 * h.max()), axis=0))[0]
+    assert inner.size > 200
+    tg = inner[:300]
+    on = oracle.forward(x, h, d["m"], v, d["u"], L, targets=tg, want=("dvdt", "dudt"))
+    off = oracle.forward(x, h, d["m"], v, d["u"], L, targets=tg, params=_params(Cl=0.0, Cq=0.0),
+                         want=("dvdt", "dudt"))
+    assert np.allclose(on["dvdt"], off["dvdt"], rtol=1e-13, atol=1e-13 * np.abs(off["dvdt"]).max())
+    assert np.allclose(on["dudt"], off["dudt"], rtol=1e-13, atol=1e-13 * np.abs(off["dudt"]).max())
+    vc = -v
+    on = oracle.forward(x, h, d["m"], vc, d["u"], L, targets=tg, params=_params(limiter=0),
+                        want=("dudt",))
+    off = oracle.forward(x, h, d["m"], vc, d["u"], L, targets=tg, params=_params(Cl=0.0, Cq=0.0),
+                         want=("dudt",))
+    assert (on["dudt"] > off["dudt"]).mean() > 0.95  # viscous heating in compression
+
+
+def test_target_mode_equals_whole_box(lognormal32):
+    d = lognormal32
+    full = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"])
+    tg = np.array([0, 5, 777, 32767, 12345])
+    sub = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], targets=tg)
+    for k in ("V", "coef", "rho", "gradv", "dvdt", "dudt"):
+        assert np.array_equal(sub[k], full[k][..., tg]), k
+
+
+# ---------------------------------------------------------------- JVP
+def test_jvp_matches_central_finite_differences(lognormal32):
+    """Dual-number tangents agree with central differences of the FP64 forward.
+
+    Distinct smoothing lengths keep the primal point off the kink of
+    min(r/h_i, r/h_j) in the near-field damping (equal h would sit on it).
+    """
+    d = lognormal32
+    x, h, m, v, u, L = d["x"], d["h"], d["m"], d["v"], d["u"], d["L"]
+    rng = np.random.default_rng(7)
+    tx = rng.normal(size=x.shape) * 1e-3
+    tv = rng.normal(size=v.shape) * 1e-1
+    tu = rng.normal(size=u.shape) * u * 0.1
+    th = rng.normal(size=h.shape) * h * 0.01
+    tg = np.arange(0, h.shape[0], 331)
+    prim, tan = oracle.jvp(x, h, m, v, u, L, tx=tx, tv=tv, tu=tu, th=th, targets=tg,
+                           want=("V", "coef", "rho", "gradv", "dvdt", "dudt"))
+    eps = 1e-6
+
+    def f(s):
+        return oracle.forward(np.mod(x + s * tx, L), h + s * th, m, v + s * tv, u + s * tu, L,
+                              targets=tg, want=("V", "coef", "rho", "gradv", "dvdt", "dudt"))
+    fp, fm = f(eps), f(-eps)
+    for k in ("V", "coef", "rho", "gradv", "dvdt", "dudt"):
+        fd = (fp[k] - fm[k]) / (2 * eps)
+        rel = np.linalg.norm(fd - tan[k]) / np.linalg.norm(fd)
+        assert rel < 1e-6, (k, rel)
+        assert np.array_equal(prim[k], oracle.forward(x, h, m, v, u, L, targets=tg,
+                                                      want=(k,))[k])
+
+
+# ---------------------------------------------------------------- errors
+def test_domain_and_singular_statuses():
+    x = np.array([[0.1, 0.5], [0.2, 0.5], [0.3, 0.5]])
+    h = np.array([0.05, 0.05])
+    m = np.ones(2)
+    o = oracle.forward(x, h, m, L=1.0, want=("coef",))
+    assert o["status"] == 6 and o["nsingular"][0] == 2   # isolated particles: m2 = 0
+    assert np.all(o["coef"][0] == 1) and np.all(o["coef"][1:] == 0)
+    with pytest.raises(ValueError, match="domain"):
+        oracle.forward(np.array([[1.0], [0.2], [0.2]]), np.array([0.1]), np.ones(1), L=1.0)
+    with pytest.raises(ValueError, match="domain"):
+        oracle.forward(np.array([[0.5], [0.2], [0.2]]), np.array([0.5]), np.ones(1), L=1.0)
+    with pytest.raises(ValueError, match="non-finite"):
+        oracle.forward(np.array([[np.nan], [0.2], [0.2]]), np.array([0.1]), np.ones(1), L=1.0)
+
+
+def test_paper_neighbor_numbers():
+    """App. A.2: n_h = 4 gives about 268 neighbors, n_h = 2.25 about 48."""
+    for nh, key in ((GOLD["gas_nh"]["value"], "gas_neighbors"), (GOLD["star_nh"]["value"], "star_neighbors")):
+        assert round(4 * np.pi / 3 * nh ** 3) == GOLD[key]["value"]
