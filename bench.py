@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark: CRKSPH pair interactions per second on GB300.
+
+One step = one pass of the whole hot path on one batch of synthetic gas:
+cell build (sort, tree, neighbor lists) -> volume and RK coefficients ->
+density, velocity gradient and pair rates -> adjoint of the rates.  The unit is
+the ordered gather pair (j != i, |x_ij| < h_i) counted once per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead (the arm the GPU path is compared against).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "CRKSPH pair interactions/s (fwd+adjoint step) on 1 GB300"
+UNIT = "pair interactions/s"
+WORKLOAD = "lognormal64"
+WORKLOAD_DESC = ("64^3 = 262,144 gas particles, lognormal density (P(k)~k^-2 field, variance 1.5, "
+                 "seed 1), h for 100+-10 neighbors, u lognormal over 3 decades, periodic unit box")
+
+# Algorithmic flops per unit of each sweep (fused multiply-add = 2 flops),
+# counted from the formulas the kernels evaluate; units are ordered gather
+# pairs (b1, b2, c1) or ordered union pairs (c2).
+FLOPS_PER_PAIR = {"b1_volume": 31, "b2_moments": 114, "c1_density": 117, "c2_rates": 251}
+UNIT_OF = {"b1_volume": "gather", "b2_moments": "gather", "c1_density": "gather",
+           "c2_rates": "union"}
+# FP32 lanes x 2 flops x SMs x max SM clock (152 SMs, 128 FP32 lanes/SM, 2070 MHz)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0, out_dir=None):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = None
+        self.out_dir = out_dir
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv", prefix="clocks_")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv",
+                 "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh.read().splitlines()[1:]:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm = float(parts[1].split()[0])
+                    smax = float(parts[2].split()[0])
+                except ValueError:
+                    continue
+                rows.append((sm, smax, parts[5], parts[6], parts[7], parts[8]))
+        if self.out_dir:
+            try:
+                os.makedirs(self.out_dir, exist_ok=True)
+                os.replace(self.path, os.path.join(self.out_dir, "clocks.csv"))
+            except OSError:
+                pass
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world):
+    import torch
+    from paper_2511_21921_gb300 import synth
+    from paper_2511_21921_gb300 import _lib as L
+    from paper_2511_21921_gb300.solver import Solver
+
+    dev = torch.device("cuda", _env_int("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    d = synth.load(args.workload)
+    n = d["h"].shape[0]
+    prec = args.precision
+    dt = torch.float32 if prec == "mixed" else torch.float64
+    gx_h, gu_h = synth.cotangents(n, seed=4)
+    # pinned host copies (end-to-end leg) and resident device copies
+    host = {"x": torch.tensor(d["x"], dtype=torch.float64).pin_memory()}
+    for k in ("h", "m", "u"):
+        host[k] = torch.tensor(d[k], dtype=dt).pin_memory()
+    host["v"] = torch.tensor(d["v"], dtype=dt).pin_memory()
+    host["ga"] = torch.tensor(gx_h, dtype=dt).pin_memory()
+    host["gu"] = torch.tensor(gu_h, dtype=dt).pin_memory()
+    dv = {k: t.to(dev) for k, t in host.items()}
+    s = Solver(n, 1, prec, device=dev)
+    s.cell_build(dv["x"], dv["h"], check=True)  # sizes the neighbor lists once
+    st0 = s.stats()
+    pairs = st0["gather_pairs"]
+    upairs = st0["union_pairs"]
+    outs = (torch.empty((3, n), dtype=dt, device=dev), torch.empty(n, dtype=dt, device=dev))
+    grads = tuple(torch.empty(sh, dtype=dt, device=dev) for sh in ((3, n), (3, n), (n,), (n,)))
+    with_adj = not args.fwd_only
+
+    def step(src):
+        s.cell_build(src["x"], src["h"], check=False)
+        s.moments(src["m"])
+        s.rates(src["v"], src["u"], out=outs)
+        if with_adj:
+            s.adjoint(src["v"], src["u"], src["ga"], src["gu"], recompute=False, out=grads)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step(dv)
+    torch.cuda.synchronize()
+    if s.poll() != 0:
+        raise RuntimeError("device status set during warm-up")
+
+    def timed(fn, k_steps, flush_l2=True):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k_steps)]
+        for k in range(k_steps):
+            if flush_l2:
+                flush.fill_(k & 0xff)
+            evs[k][0].record(stream)
+            fn()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    sampler = ClockSampler(dev.index, out_dir=os.path.join(ROOT, "gpurun_out") if
+                           os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    l0 = s.stats()["launches"]
+    ms = timed(lambda: step(dv), args.steps)
+    launches = s.stats()["launches"] - l0
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = sum(ms) / len(ms)
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+    status = s.poll()
+
+    # end to end: pinned host inputs -> device, step, results -> pinned host
+    out_h = (torch.empty((3, n), dtype=dt).pin_memory(), torch.empty(n, dtype=dt).pin_memory())
+    grad_h = tuple(torch.empty(g.shape, dtype=dt).pin_memory() for g in grads)
+    stage = {k: torch.empty_like(t) for k, t in dv.items()}
+
+    def e2e_step():
+        for k, t in host.items():
+            stage[k].copy_(t, non_blocking=True)
+        step(stage)
+        out_h[0].copy_(outs[0], non_blocking=True)
+        out_h[1].copy_(outs[1], non_blocking=True)
+        if with_adj:
+            for a, b in zip(grad_h, grads):
+                a.copy_(b, non_blocking=True)
+
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = sum(t.numel() * t.element_size() for t in out_h)
+    if with_adj:
+        d2h += sum(t.numel() * t.element_size() for t in grad_h)
+    e2e_ms = timed(e2e_step, max(3, args.steps // 4))
+    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+
+    # per-kernel durations (library CUDA events on the launching stream)
+    L.crk_timing_enable(s.plan, True)
+    kt = {}
+    nk = max(3, min(args.steps, 20))
+    for k in range(nk):
+        flush.fill_(k & 0xff)
+        step(dv)
+        for name, t in L.crk_timing_read(s.plan):
+            kt.setdefault(name, []).append(t)
+    L.crk_timing_enable(s.plan, False)
+    kmean = {k: sum(v) / len(v) for k, v in kt.items()}
+    fwd_names = ("build.check", "build.keys_sort", "build.tree", "build.lists", "pack_b1",
+                 "b1_volume", "b2_moments", "pack_c1", "c1_density", "c2_rates")
+    fwd_ms = sum(kmean.get(k, 0.0) for k in fwd_names)
+    units = {"gather": pairs, "union": upairs}
+    dom = max((k for k in kmean if k in FLOPS_PER_PAIR), key=lambda k: kmean[k])
+    flops = FLOPS_PER_PAIR[dom] * units[UNIT_OF[dom]]
+    achieved = flops / (kmean[dom] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
+                "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "flops_per_pair": FLOPS_PER_PAIR[dom], "pairs": units[UNIT_OF[dom]],
+                "kernel_ms": round(kmean[dom], 4)}
+    res = {
+        "metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
+        "value": pairs * world / (step_ms * 1e-3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "name": args.workload, "n": n,
+                   "gather_pairs": pairs, "union_pairs": upairs,
+                   "precision": prec, "step": "build+moments+rates" + ("+adjoint" if with_adj
+                                                                       else ""),
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replica x{world}" if world > 1 else "1 GPU"},
+        "e2e": {"value": pairs * world / (e2e_mean * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "fwd_pairs_per_s": pairs / (fwd_ms * 1e-3) if fwd_ms > 0 else None,
+        "kernel_ms": {k: round(v, 4) for k, v in sorted(kmean.items())},
+        "roofline": roofline,
+        "clocks": clocks,
+        "device_status": status,
+    }
+    if args.fp64_compare and world == 1 and prec == "mixed":
+        res["fp64_gpu"] = fp64_compare(args, d, dev)
+        if res["fp64_gpu"]:
+            res["speedup_vs_fp64_gpu"] = round(step_ms and res["fp64_gpu"]["ms_per_step"] /
+                                               step_ms, 2)
+    return res, pairs
+
+
+def fp64_compare(args, d, dev):
+    """The plain FP64 GPU form on the same workload (same step, fewer repeats)."""
+    import torch
+    from paper_2511_21921_gb300.solver import Solver
+    from paper_2511_21921_gb300 import synth
+    n = d["h"].shape[0]
+    t64 = {k: torch.tensor(d[k], dtype=torch.float64, device=dev) for k in ("x", "h", "m", "u",
+                                                                           "v")}
+    ga, gu = synth.cotangents(n, seed=4)
+    t64["ga"] = torch.tensor(ga, dtype=torch.float64, device=dev)
+    t64["gu"] = torch.tensor(gu, dtype=torch.float64, device=dev)
+    s = Solver(n, 1, "fp64", device=dev)
+    s.cell_build(t64["x"], t64["h"], check=True)
+
+    def step():
+        s.cell_build(t64["x"], t64["h"], check=False)
+        s.moments(t64["m"])
+        s.rates(t64["v"], t64["u"])
+        if not args.fwd_only:
+            s.adjoint(t64["v"], t64["u"], t64["ga"], t64["gu"], recompute=False)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    k = max(2, min(5, args.steps))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(k):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / k
+    return {"ms_per_step": round(ms, 4), "value": s.stats()["gather_pairs"] / (ms * 1e-3)}
+
+
+# ---------------------------------------------------------------------------- CPU arm
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_pass(d, with_derivative=True):
+    """One oracle evaluation of the step: forward values and, for the adjoint
+    part, the oracle's derivative pass (forward-mode JVP; it has no reverse)."""
+    import oracle
+    n = d["h"].shape[0]
+    t0 = time.perf_counter()
+    if with_derivative:
+        rng = np.random.default_rng(0)
+        oracle.jvp(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], tx=rng.normal(size=(3, n)) * 1e-4,
+                   want=("dvdt", "dudt"))
+    else:
+        oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], want=("dvdt", "dudt"))
+    return time.perf_counter() - t0
+
+
+def _oracle_pairs(d):
+    import oracle
+    o = oracle.forward(d["x"], d["h"], d["m"], L=d["L"], want=("kgather",))
+    return int(o["kgather"].sum())
+
+
+def cpu_baseline(args):
+    """The oracle as it stands on the host cores: the whole benchmark workload,
+    one forward-mode pass with one JVP (about 5-20 s)."""
+    from paper_2511_21921_gb300 import synth
+    import oracle
+    d = synth.load(args.workload)
+    pairs = _oracle_pairs(d)
+    t = oracle_pass(d, not args.fwd_only)
+    return {"value": pairs / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"whole {args.workload} workload ({pairs} gather pairs), one oracle "
+                      "forward pass with one forward-mode derivative (JVP), FP64, OpenMP "
+                      "over particles",
+            "seconds": round(t, 3)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed step by step on the host cores."""
+    from paper_2511_21921_gb300 import synth
+    import oracle
+    oracle.build()
+    budget = 150.0 / max(1, args.steps + args.warmup)  # seconds per step
+    name = args.workload
+    d = synth.load(name)
+    probe = oracle_pass(d, not args.fwd_only)
+    sample = f"whole {name} workload"
+    if probe > budget and name == "lognormal64":
+        name = "lognormal32"  # same generator and statistics, 1/8 of the particles
+        d = synth.load(name)
+        sample = ("lognormal32: same generator and statistics as lognormal64, 1/8 of the "
+                  "particles (per-step budget)")
+    pairs = _oracle_pairs(d)
+    for _ in range(args.warmup):
+        oracle_pass(d, not args.fwd_only)
+    ts = [oracle_pass(d, not args.fwd_only) for _ in range(args.steps)]
+    mean = sum(ts) / len(ts)
+    val = pairs / mean
+    cores = oracle.num_threads()
+    return {
+        "impl": "reference", "metric": METRIC, "unit": UNIT, "value": val,
+        "higher_is_better": True, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(mean * 1e3, 3), "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "name": args.workload, "sample": sample,
+                   "gather_pairs_per_step": pairs},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample + "; forward values plus one JVP per step"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+# ---------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--fwd-only", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-compare", action="store_true", default=True)
+    ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res, _ = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            res["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

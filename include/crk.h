@@ -1,0 +1,182 @@
+/* crk.h -- C ABI of the GB300 CRKSPH neighbor-sum library (libcrk).
+ *
+ * The library evaluates the hydrodynamic hot path of CRK-HACC (arXiv
+ * 2511.21921) for gas particles in periodic boxes:
+ *
+ *   crk_cell_build  -- Morton sort, bucket tree and per-particle neighbor
+ *                      lists (the paper's GPU tree with few rebuilds, Sec. 2.7).
+ *   crk_moments     -- gas volume V (App. A.2, Eq. Vg), geometric moments and
+ *                      reproducing-kernel coefficients A, B, grad A, grad B
+ *                      (App. A.1, Eq. RK; closed forms from the reproducing
+ *                      conditions of the CRKSPH formulation the paper cites).
+ *   crk_rates       -- RK density (Sec. 2.4.2, Eq. rhow, gas only), velocity
+ *                      gradient (App. A.1, Eq. gradv), ideal-gas EOS with
+ *                      gamma from the parameters (5/3, Sec. 2.3), relaxation
+ *                      flag (App. A.1), and pairwise momentum and compatible
+ *                      energy rates with limited artificial viscosity (Sec. 2.1).
+ *   crk_adjoint     -- vector-Jacobian product of the rates with respect to
+ *                      positions, velocities, internal energies and smoothing
+ *                      lengths (no counterpart in the paper; it gives the
+ *                      subgrid calibration of Sec. 3 a gradient).
+ *
+ * Conventions shared by every entry point:
+ *  - Device pointers are owned by the caller; the library never allocates
+ *    device or pinned memory.  All scratch lives in the caller's workspace
+ *    `ws` of at least crk_workspace_size() bytes (256-byte aligned).
+ *  - Arrays are structure-of-arrays in the caller's particle order:
+ *    a vector field of n particles is [3][n] (component-major); n <= 2^30.
+ *  - Element type: positions `x` and box sides are always double.  Every other
+ *    real array is double when params.precision == CRK_FP64 and float when
+ *    params.precision == CRK_MIXED32.
+ *  - Calls are asynchronous on `stream` and never synchronise the host, so a
+ *    sequence of them can be captured in a CUDA graph -- except
+ *    crk_status_poll, crk_stats and crk_neighbors_csr, which synchronise.
+ *  - Argument errors are returned immediately.  Data errors found on the
+ *    device (x outside [0, L), h >= L/2, non-finite input, singular second
+ *    moment, list capacity exceeded) set a device status word that
+ *    crk_status_poll returns (and clears; crk_cell_build also clears it when
+ *    it starts); outputs of a call that set it are undefined.
+ *    No kernel traps or waits without a bound.
+ */
+#ifndef CRK_H
+#define CRK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* crk_stream_t; /* a cudaStream_t; NULL = legacy default */
+
+typedef enum {
+  CRK_OK = 0,
+  CRK_EINVAL = 1,      /* bad argument (NULL pointer, size, parameter) */
+  CRK_ENOMEM = 2,      /* workspace too small or neighbor-list capacity exceeded */
+  CRK_ECUDA = 3,       /* a CUDA runtime call failed */
+  CRK_EDOMAIN = 4,     /* some x outside [0, L) or h outside (0, L/2) */
+  CRK_ENONFINITE = 5,  /* NaN or Inf in an input */
+  CRK_ESINGULAR = 6,   /* second moment m2 singular for some particle (it falls back to A=1, B=0) */
+  CRK_ETIMEOUT = 7,    /* a bounded device wait gave up */
+  CRK_ESTATE = 8       /* call out of order (e.g. crk_rates before crk_moments) */
+} crk_status;
+
+typedef enum {
+  CRK_FP64 = 0,    /* every sum and pair term in double (the plain FP64 form) */
+  CRK_MIXED32 = 1  /* float pair arithmetic and accumulation; double-equivalent
+                      minimum-image separations; double 3x3 inverse of m2 */
+} crk_precision;
+
+typedef struct {
+  double gamma;     /* adiabatic index; 5/3 for a monatomic ideal gas (Sec. 2.3) */
+  double Cl, Cq;    /* linear / quadratic artificial-viscosity coefficients */
+  double eps2;      /* softening of the viscosity denominator |eta|^2 + eps2 */
+  double eta_crit;  /* near-field damping applies when min(r/h_i, r/h_j) < eta_crit */
+  double eta_fold;  /* width of the near-field damping exp(-((eta-eta_crit)/eta_fold)^2) */
+  double relax_dt;  /* relaxation time step (App. A.1); 0 turns relaxation off */
+  int32_t limiter;  /* 1: velocity-gradient limiter on the viscosity; 0: off */
+  int32_t precision;/* crk_precision */
+  int32_t nbr_cap;  /* neighbor-list slots per particle reserved in the workspace; 0 = 160 */
+  int32_t block_threads; /* threads per block of the pair sweeps; 0 = autotuned default */
+  int32_t blocks_per_sm; /* resident blocks per SM for the persistent sweeps; 0 = default */
+  int32_t reserved[3];
+} crk_params;
+
+typedef struct crk_plan crk_plan;
+
+/* Fill `p` with the library defaults: gamma = 5/3, Cl = 2, Cq = 1, eps2 = 0.01,
+ * eta_crit = 1/n_h for n_h = (3*100/(4 pi))^(1/3), eta_fold = 0.2, relaxation
+ * off, limiter on, CRK_MIXED32.  Host only. */
+void crk_params_default(crk_params* p);
+
+/* Create a plan for up to n_max particles in up to n_boxes_max boxes.  The plan
+ * owns host metadata only (sizes, tuned launch shapes, the state of the
+ * workspace it last built).  Host only; CRK_EINVAL on bad sizes/parameters. */
+crk_status crk_plan_create(const crk_params* params, int64_t n_max, int32_t n_boxes_max,
+                           crk_plan** out);
+void crk_plan_destroy(crk_plan* plan);
+
+/* Bytes of workspace needed for n particles in n_boxes boxes.  Host only. */
+crk_status crk_workspace_size(const crk_plan* plan, int64_t n, int32_t n_boxes, size_t* bytes);
+
+/* (a) Cell-list build.  box_off: device int64[n_boxes+1], box_off[0] = 0,
+ * box_off[n_boxes] = n, non-decreasing: particles of box b are
+ * [box_off[b], box_off[b+1]).  box_L: device double[n_boxes], side of each
+ * periodic box [0, L)^3.  x: device double[3][n].  h: device real[n],
+ * 0 < h < L/2.  Sorts the particles by (box, Morton key), builds the bucket
+ * tree and the union neighbor lists U(i) = {j != i, |x_ij| < max(h_i, h_j)}
+ * with flags for the gather set (|x_ij| < h_i).  Stores everything in ws. */
+crk_status crk_cell_build(crk_plan* plan, crk_stream_t stream, void* ws, size_t ws_bytes,
+                          int64_t n, int32_t n_boxes, const int64_t* box_off,
+                          const double* box_L, const double* x, const void* h);
+
+/* (b) Volume and reproducing-kernel coefficients.  m: device real[n] masses.
+ * V_out: optional device real[n].  coef_out: optional device real[16][n]
+ * holding A, B[3], gradA[3], gradB[3][3] (gradB[g][a] = d B^a / d x^g). */
+crk_status crk_moments(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
+                       void* V_out, void* coef_out);
+
+/* (c) Rates.  v: device real[3][n], u: device real[n] (specific internal
+ * energy, >= 0).  Outputs dvdt: real[3][n], dudt: real[n]; optional rho_out:
+ * real[n]; optional gradv_out: real[9][n] with gradv[a*3+b] = d v^a / d x^b. */
+crk_status crk_rates(crk_plan* plan, crk_stream_t stream, void* ws, const void* v, const void* u,
+                     void* dvdt, void* dudt, void* rho_out, void* gradv_out);
+
+/* (d) Adjoint.  Given cotangents g_dvdt real[3][n] and g_dudt real[n] of the
+ * rates, accumulate nothing and write the vector-Jacobian products
+ * g_x real[3][n], g_v real[3][n], g_u real[n], g_h real[n].  Neighbor sets,
+ * image shifts, relaxation flags and limiter branches are held at the primal
+ * point.  recompute = 1 re-evaluates the per-particle forward state (volume,
+ * coefficients, density, velocity gradient) from v, u and the masses of the
+ * last crk_moments; recompute = 0 reuses the state the last crk_rates left in
+ * ws (same inputs).  No per-pair data is stored. */
+crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void* v, const void* u,
+                       const void* g_dvdt, const void* g_dudt, void* g_x, void* g_v, void* g_u,
+                       void* g_h, int32_t recompute);
+
+/* Test/inspection: the neighbor sets of the last build as CSR in caller order.
+ * mode 0: gather set G(i) without the particle itself; mode 1: union set U(i).
+ * row_ptr: device int64[n+1]; col: device int32[cap], sorted within a row.
+ * *nnz (host) receives the total; CRK_ENOMEM if it exceeds cap.  Synchronises. */
+crk_status crk_neighbors_csr(crk_plan* plan, crk_stream_t stream, void* ws, int32_t mode,
+                             int64_t* row_ptr, int32_t* col, int64_t cap, int64_t* nnz);
+
+typedef struct {
+  int64_t n, n_boxes;
+  int64_t gather_pairs;   /* sum_i |G(i)| - n: ordered pairs j != i with r < h_i */
+  int64_t union_pairs;    /* sum_i |U(i)| */
+  int64_t list_slots;     /* neighbor-list slots used (with per-warp padding) */
+  int64_t list_capacity;  /* slots available in the workspace */
+  int64_t tree_nodes;
+  int64_t launches;       /* kernels this plan has launched since it was created (host count) */
+  int32_t status;         /* device status word (not cleared) */
+  int32_t reserved;
+} crk_stats;
+
+/* Statistics of the last build.  Synchronises `stream`. */
+crk_status crk_stats_get(crk_plan* plan, crk_stream_t stream, void* ws, crk_stats* out);
+
+/* Synchronise `stream`, return the device status word in *device_status and
+ * clear it. */
+crk_status crk_status_poll(crk_plan* plan, crk_stream_t stream, void* ws,
+                           crk_status* device_status);
+
+const char* crk_status_string(crk_status s);
+
+/* Per-kernel timing.  While enabled, every neighbor sweep and build phase the
+ * plan launches is bracketed by CUDA events on its stream (up to 256 records,
+ * oldest first).  crk_timing_read synchronises on the last event, writes up to
+ * `cap` records (name, milliseconds) and clears the list.  Host only apart
+ * from the event records; enabling adds two event records per launch. */
+typedef struct {
+  char name[24];
+  float ms;
+} crk_kernel_time;
+crk_status crk_timing_enable(crk_plan* plan, int32_t enable);
+crk_status crk_timing_read(crk_plan* plan, crk_kernel_time* out, int32_t cap, int32_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRK_H */

@@ -1,0 +1,183 @@
+"""ctypes binding of libcrk (include/crk.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Importing this module loads ``_build/libcrk.so`` and raises if it is
+missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+from . import build as _build
+
+CRK_OK, CRK_EINVAL, CRK_ENOMEM, CRK_ECUDA, CRK_EDOMAIN, CRK_ENONFINITE, CRK_ESINGULAR, \
+    CRK_ETIMEOUT, CRK_ESTATE = range(9)
+CRK_FP64, CRK_MIXED32 = 0, 1
+
+STATUS_NAMES = {0: "CRK_OK", 1: "CRK_EINVAL", 2: "CRK_ENOMEM", 3: "CRK_ECUDA", 4: "CRK_EDOMAIN",
+                5: "CRK_ENONFINITE", 6: "CRK_ESINGULAR", 7: "CRK_ETIMEOUT", 8: "CRK_ESTATE"}
+
+
+class crk_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("Cl", C.c_double), ("Cq", C.c_double),
+                ("eps2", C.c_double), ("eta_crit", C.c_double), ("eta_fold", C.c_double),
+                ("relax_dt", C.c_double), ("limiter", C.c_int32), ("precision", C.c_int32),
+                ("nbr_cap", C.c_int32), ("block_threads", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+class crk_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_boxes", C.c_int64), ("gather_pairs", C.c_int64),
+                ("union_pairs", C.c_int64), ("list_slots", C.c_int64),
+                ("list_capacity", C.c_int64), ("tree_nodes", C.c_int64),
+                ("launches", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
+class crk_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("ms", C.c_float)]
+
+
+class CRKError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = int(code)
+        super().__init__(f"{where}: {STATUS_NAMES.get(self.code, self.code)} "
+                         f"({crk_status_string(self.code)})")
+
+
+_VP = C.c_void_p
+_SIGS = {
+    "crk_params_default": (None, [C.POINTER(crk_params)]),
+    "crk_plan_create": (C.c_int, [C.POINTER(crk_params), C.c_int64, C.c_int32, C.POINTER(_VP)]),
+    "crk_plan_destroy": (None, [_VP]),
+    "crk_workspace_size": (C.c_int, [_VP, C.c_int64, C.c_int32, C.POINTER(C.c_size_t)]),
+    "crk_cell_build": (C.c_int, [_VP, _VP, _VP, C.c_size_t, C.c_int64, C.c_int32, _VP, _VP, _VP,
+                                 _VP]),
+    "crk_moments": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "crk_rates": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "crk_adjoint": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int32]),
+    "crk_neighbors_csr": (C.c_int, [_VP, _VP, _VP, C.c_int32, _VP, _VP, C.c_int64,
+                                    C.POINTER(C.c_int64)]),
+    "crk_stats_get": (C.c_int, [_VP, _VP, _VP, C.POINTER(crk_stats)]),
+    "crk_status_poll": (C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_int)]),
+    "crk_status_string": (C.c_char_p, [C.c_int]),
+    "crk_timing_enable": (C.c_int, [_VP, C.c_int32]),
+    "crk_timing_read": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_int32)]),
+}
+
+_lib = None
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libcrk.so (building it first when allowed); raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build_library()
+    if not os.path.exists(path):
+        raise ImportError(f"libcrk.so not built at {path}; run paper_2511_21921_gb300.build")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_symbols() -> list[str]:
+    """Function names declared in include/crk.h."""
+    with open(os.path.join(_build.INCLUDE, "crk.h")) as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(crk_[a-z_]+)\s*\(", src)))
+
+
+def crk_status_string(code: int) -> str:
+    s = load().crk_status_string(int(code))
+    return s.decode() if s else "?"
+
+
+def check(code: int, where: str) -> None:
+    if code != CRK_OK:
+        raise CRKError(code, where)
+
+
+# thin same-name wrappers -----------------------------------------------------
+def crk_params_default() -> crk_params:
+    p = crk_params()
+    load().crk_params_default(C.byref(p))
+    return p
+
+
+def crk_plan_create(params: crk_params, n_max: int, n_boxes_max: int) -> int:
+    h = _VP()
+    check(load().crk_plan_create(C.byref(params), int(n_max), int(n_boxes_max), C.byref(h)),
+          "crk_plan_create")
+    return h.value
+
+
+def crk_plan_destroy(plan: int) -> None:
+    if plan:
+        load().crk_plan_destroy(_VP(plan))
+
+
+def crk_workspace_size(plan: int, n: int, n_boxes: int) -> int:
+    b = C.c_size_t()
+    check(load().crk_workspace_size(_VP(plan), int(n), int(n_boxes), C.byref(b)),
+          "crk_workspace_size")
+    return int(b.value)
+
+
+def crk_cell_build(plan, stream, ws, ws_bytes, n, n_boxes, box_off, box_L, x, h) -> int:
+    return load().crk_cell_build(_VP(plan), _VP(stream), _VP(ws), int(ws_bytes), int(n),
+                                 int(n_boxes), _VP(box_off), _VP(box_L), _VP(x), _VP(h))
+
+
+def crk_moments(plan, stream, ws, m, V_out=None, coef_out=None) -> int:
+    return load().crk_moments(_VP(plan), _VP(stream), _VP(ws), _VP(m), _VP(V_out),
+                              _VP(coef_out))
+
+
+def crk_rates(plan, stream, ws, v, u, dvdt, dudt, rho_out=None, gradv_out=None) -> int:
+    return load().crk_rates(_VP(plan), _VP(stream), _VP(ws), _VP(v), _VP(u), _VP(dvdt),
+                            _VP(dudt), _VP(rho_out), _VP(gradv_out))
+
+
+def crk_adjoint(plan, stream, ws, v, u, g_dvdt, g_dudt, g_x, g_v, g_u, g_h, recompute) -> int:
+    return load().crk_adjoint(_VP(plan), _VP(stream), _VP(ws), _VP(v), _VP(u), _VP(g_dvdt),
+                              _VP(g_dudt), _VP(g_x), _VP(g_v), _VP(g_u), _VP(g_h),
+                              int(recompute))
+
+
+def crk_neighbors_csr(plan, stream, ws, mode, row_ptr, col, cap):
+    nnz = C.c_int64()
+    rc = load().crk_neighbors_csr(_VP(plan), _VP(stream), _VP(ws), int(mode), _VP(row_ptr),
+                                  _VP(col), int(cap), C.byref(nnz))
+    return rc, int(nnz.value)
+
+
+def crk_stats_get(plan, stream, ws) -> crk_stats:
+    s = crk_stats()
+    check(load().crk_stats_get(_VP(plan), _VP(stream), _VP(ws), C.byref(s)), "crk_stats_get")
+    return s
+
+
+def crk_status_poll(plan, stream, ws) -> int:
+    v = C.c_int()
+    check(load().crk_status_poll(_VP(plan), _VP(stream), _VP(ws), C.byref(v)), "crk_status_poll")
+    return int(v.value)
+
+
+def crk_timing_enable(plan, enable: bool) -> None:
+    check(load().crk_timing_enable(_VP(plan), 1 if enable else 0), "crk_timing_enable")
+
+
+def crk_timing_read(plan) -> list[tuple[str, float]]:
+    buf = (crk_kernel_time * 256)()
+    cnt = C.c_int32()
+    check(load().crk_timing_read(_VP(plan), buf, 256, C.byref(cnt)), "crk_timing_read")
+    return [(buf[k].name.decode(), float(buf[k].ms)) for k in range(cnt.value)]

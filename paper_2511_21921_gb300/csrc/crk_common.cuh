@@ -1,0 +1,209 @@
+// crk_common.cuh -- internal definitions shared by the libcrk translation units:
+// workspace layout, device status word, precision traits, minimum-image
+// separations and the Wendland C4 kernel.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "../../include/crk.h"
+
+namespace crk {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarp = 32;
+constexpr int kBucket = 8;          // particles per tree leaf (bucket)
+constexpr int kSortTile = 4096;     // keys per radix-sort tile
+constexpr int kSortThreads = 256;
+constexpr int kStackDepth = 96;     // tree traversal stack (depth <= 64 key bits + 30 index bits)
+constexpr uint32_t kIdxMask = 0x3fffffffu;
+constexpr uint32_t kGatherBit = 0x80000000u;   // j in G(i):  r < h_i
+constexpr uint32_t kScatterBit = 0x40000000u;  // i in G(j):  r < h_j
+constexpr uint32_t kSentinel = 0xffffffffu;
+
+// Work-queue counters, one per persistent sweep of a call.
+enum Queue {
+  Q_B1 = 0, Q_B2, Q_C1, Q_C2, Q_A_C2, Q_A_C1, Q_A_B2, Q_A_B1, Q_COUNT_, Q_FILL_, Q_N = 16
+};
+
+struct DevHeader {
+  int32_t status;
+  int32_t pad0;
+  unsigned long long slots_needed;
+  unsigned long long gather_pairs;
+  unsigned long long union_pairs;
+  unsigned long long nsingular;
+  int32_t queue[Q_N];
+  int32_t pad1[16];
+};
+
+__device__ __forceinline__ void set_status(DevHeader* h, int code) {
+  atomicCAS(&h->status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// precision traits: float records carry positions as double-float (hi, lo)
+// pairs (6 words); double records carry them as plain doubles (3 words).
+// ---------------------------------------------------------------------------
+template <class R> struct Prec;
+template <> struct Prec<float> {
+  static constexpr int XW = 6;      // words of position per record
+  static constexpr int VEC = 4;     // words per vector load (float4)
+  using V4 = float4;
+};
+template <> struct Prec<double> {
+  static constexpr int XW = 3;
+  static constexpr int VEC = 2;     // double2
+  using V4 = double2;
+};
+
+constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Record layouts (words of R per particle), each padded to whole vector loads.
+template <class R> struct Rec {
+  static constexpr int XW = Prec<R>::XW;
+  static constexpr int VEC = Prec<R>::VEC;
+  // b1 (volume): x, m
+  static constexpr int B1_M = XW, B1 = round_up(XW + 1, VEC);
+  // b2 (moments): x, V
+  static constexpr int B2_V = XW, B2 = round_up(XW + 1, VEC);
+  // c1 (density, grad v): x, V, m, v[3]
+  static constexpr int C1_V = XW, C1_M = XW + 1, C1_VEL = XW + 2, C1 = round_up(XW + 5, VEC);
+  // c2 (rates): x, ih, V, P, qa, qb, flag, v[3], A, B[3], dA[3], dB[9], gv[9]
+  static constexpr int C2_IH = XW, C2_V = XW + 1, C2_P = XW + 2, C2_QA = XW + 3,
+                       C2_QB = XW + 4, C2_FLAG = XW + 5, C2_VEL = XW + 6, C2_A = XW + 9,
+                       C2_B = XW + 10, C2_DA = XW + 13, C2_DB = XW + 16, C2_GV = XW + 25,
+                       C2 = round_up(XW + 34, VEC);
+};
+
+// vectorised load of a record of NW words (NW a multiple of the vector width)
+template <int NW>
+__device__ __forceinline__ void load_rec(const float* __restrict__ base, int64_t s, float* out) {
+  const float4* p = reinterpret_cast<const float4*>(base + s * NW);
+#pragma unroll
+  for (int k = 0; k < NW / 4; ++k) {
+    float4 t = __ldg(p + k);
+    out[4 * k + 0] = t.x; out[4 * k + 1] = t.y; out[4 * k + 2] = t.z; out[4 * k + 3] = t.w;
+  }
+}
+template <int NW>
+__device__ __forceinline__ void load_rec(const double* __restrict__ base, int64_t s, double* out) {
+  const double2* p = reinterpret_cast<const double2*>(base + s * NW);
+#pragma unroll
+  for (int k = 0; k < NW / 2; ++k) {
+    double2 t = __ldg(p + k);
+    out[2 * k + 0] = t.x; out[2 * k + 1] = t.y;
+  }
+}
+template <int NW>
+__device__ __forceinline__ void store_rec(float* base, int64_t s, const float* in) {
+  float4* p = reinterpret_cast<float4*>(base + s * NW);
+#pragma unroll
+  for (int k = 0; k < NW / 4; ++k)
+    p[k] = make_float4(in[4 * k + 0], in[4 * k + 1], in[4 * k + 2], in[4 * k + 3]);
+}
+template <int NW>
+__device__ __forceinline__ void store_rec(double* base, int64_t s, const double* in) {
+  double2* p = reinterpret_cast<double2*>(base + s * NW);
+#pragma unroll
+  for (int k = 0; k < NW / 2; ++k) p[k] = make_double2(in[2 * k + 0], in[2 * k + 1]);
+}
+
+// ---------------------------------------------------------------------------
+// minimum-image separation x_ij = x_i - x_j
+// ---------------------------------------------------------------------------
+// double: the plain definition, decided and computed in double.
+__device__ __forceinline__ void separation(const double* xi, const double* xj, double L,
+                                           double halfL, double* d) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double t = __dsub_rn(xi[a], xj[a]);
+    if (t > halfL) t = __dsub_rn(t, L);
+    else if (t < -halfL) t = __dadd_rn(t, L);
+    d[a] = t;
+  }
+}
+// float: positions are hi + lo double-float pairs.  hi_i - hi_j is rounded
+// once (relative error 2^-24 of the separation); wrapping by L is exact
+// (Sterbenz) because it only happens when |hi_i - hi_j| > L/2; adding the
+// low-part difference restores the bits below hi's last place.  The result
+// equals the double minimum image to about one float ulp, and x_ji = -x_ij
+// holds bit for bit.
+__device__ __forceinline__ void separation(const float* xi, const float* xj, float L,
+                                           float halfL, float* d) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float t = __fsub_rn(xi[a], xj[a]);
+    if (t > halfL) t = __fsub_rn(t, L);
+    else if (t < -halfL) t = __fadd_rn(t, L);
+    d[a] = __fadd_rn(t, __fsub_rn(xi[3 + a], xj[3 + a]));
+  }
+}
+
+template <class R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float exp_(float x) { return expf(x); }
+__device__ __forceinline__ double exp_(double x) { return exp(x); }
+
+// r = |x| from r^2 (0 for coincident points)
+template <class R> __device__ __forceinline__ R radius(R r2) {
+  return r2 > R(0) ? sqrt_(r2) : R(0);
+}
+
+// ---------------------------------------------------------------------------
+// Wendland C4 in 3-D with compact support h (q = r/h):
+//   W = c_w / h^3 (1-q)^6 (1 + 6q + 35q^2/3),  g = (1/r) dW/dr = c_g / h^5 (1-q)^5 (1 + 5q)
+// with c_w = 495/(32 pi), c_g = -(56/3) c_w.  (1-q) is clamped at 0 so both
+// vanish outside the support.
+// ---------------------------------------------------------------------------
+template <class R> struct Wend {
+  static constexpr double pi = 3.14159265358979323846;
+  static constexpr double cw = 495.0 / (32.0 * pi);
+  static constexpr double cg = -(56.0 / 3.0) * (495.0 / (32.0 * pi));
+};
+
+template <class R>
+__device__ __forceinline__ void wendland(R r, R ih, R& W, R& g) {
+  R q = r * ih;
+  R om = R(1) - q;
+  om = om > R(0) ? om : R(0);
+  R om2 = om * om;
+  R om4 = om2 * om2;
+  R ih2 = ih * ih;
+  R ih3 = ih2 * ih;
+  W = R(Wend<R>::cw) * ih3 * (om4 * om2) * (R(1) + q * (R(6) + q * R(35.0 / 3.0)));
+  g = R(Wend<R>::cg) * (ih3 * ih2) * (om4 * om) * (R(1) + R(5) * q);
+}
+
+// W(0, h) = c_w / h^3
+template <class R> __device__ __forceinline__ R wendland0(R ih) {
+  return R(Wend<R>::cw) * ih * ih * ih;
+}
+
+// ---------------------------------------------------------------------------
+// host-side workspace layout
+// ---------------------------------------------------------------------------
+struct Layout {
+  int64_t n = 0, nb = 0, nw = 0, nbk = 0, ni = 0, nt = 0, ntiles = 0, cap = 0;
+  int prec = 1;
+  size_t total = 0;
+  size_t hdr = 0, box_L = 0;
+  size_t key0 = 0, key1 = 0, val0 = 0, val1 = 0, hist = 0, scan_tmp = 0;
+  size_t perm = 0, boxid = 0, xs = 0, hs = 0, ms = 0, us = 0, vs = 0;
+  size_t aabb = 0, hmaxn = 0, brange = 0, child = 0, parent = 0, visit = 0;
+  size_t cnt_g = 0, cnt_u = 0, wlen_g = 0, wlen_u = 0, woff = 0, ell = 0;
+  size_t rec_b1 = 0, rec_b2 = 0, rec_c1 = 0, rec_c2 = 0, coef = 0, Vs = 0, rhos = 0;
+  size_t gvs = 0, Ds = 0;
+  // adjoint
+  size_t adj_ab = 0, adj_rec1 = 0, adj_rec2 = 0, adj_rec3 = 0, adj_acc = 0, adj_cbar = 0,
+         mom = 0;
+  size_t out_x = 0, out_v = 0, out_u = 0, out_h = 0;
+};
+
+size_t scan_tmp_bytes(int64_t n);
+
+}  // namespace crk

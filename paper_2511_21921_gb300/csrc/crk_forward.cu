@@ -1,0 +1,492 @@
+// crk_forward.cu -- (b) volume and RK coefficients, (c) density, velocity
+// gradient, EOS and pair rates.  Every sweep is a persistent kernel: each warp
+// takes 32 consecutive sorted particles from an atomic work queue, each lane
+// walks its own neighbor list (gather or union part) and gathers the
+// neighbor's packed record from global memory.
+#include "crk_sweep.cuh"
+
+namespace crk {
+
+// ===========================================================================
+// prologue of crk_moments: pack (x, m) records in sorted order
+// ===========================================================================
+template <class R>
+__global__ void k_pack_b1(const R* __restrict__ xs, const R* __restrict__ m,
+                          const int32_t* __restrict__ perm, int64_t n, R* __restrict__ rec,
+                          R* __restrict__ ms) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  using RC = Rec<R>;
+  R r[RC::B1];
+#pragma unroll
+  for (int k = 0; k < RC::B1; ++k) r[k] = R(0);
+  get_x(xs, n, s, r);
+  R mm = m[perm[s]];
+  r[RC::B1_M] = mm;
+  ms[s] = mm;
+  store_rec<RC::B1>(rec, s, r);
+}
+
+// ===========================================================================
+// b1: volume  V_i = m_i / sum_{j in G(i)} m_j W(r_ij, h_i)   (Eq. Vg)
+// ===========================================================================
+template <class R> struct PassB1 {
+  static constexpr bool GATHER = true;
+  static constexpr int QUEUE = Q_B1;
+  using RC = Rec<R>;
+  struct Args {
+    Common c;
+    const R* __restrict__ rec_b1;
+    const R* __restrict__ hs;
+    R* rec_b2;
+    R* Vs;
+    R* V_out;
+  };
+  struct State {
+    R x[RC::XW];
+    R ih, L, halfL, m, sum;
+  };
+  __device__ static void begin(const Args& a, int64_t s, State& st) {
+    R r[RC::B1];
+    load_rec<RC::B1>(a.rec_b1, s, r);
+#pragma unroll
+    for (int k = 0; k < RC::XW; ++k) st.x[k] = r[k];
+    st.m = r[RC::B1_M];
+    st.ih = R(1) / a.hs[s];
+    double L = a.c.box_L[a.c.boxid[s]];
+    st.L = (R)L;
+    st.halfL = (R)(0.5 * L);
+    st.sum = R(0);
+  }
+  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
+    R r[RC::B1];
+    load_rec<RC::B1>(a.rec_b1, j, r);
+    R d[3];
+    separation(st.x, r, st.L, st.halfL, d);
+    R W, g;
+    wendland(radius(dot3(d, d)), st.ih, W, g);
+    st.sum += r[RC::B1_M] * W;
+  }
+  __device__ static void end(const Args& a, int64_t s, State& st) {
+    R sum = st.sum + st.m * wendland0(st.ih);
+    R V = st.m / sum;
+    R r[RC::B2];
+#pragma unroll
+    for (int k = 0; k < RC::B2; ++k) r[k] = R(0);
+#pragma unroll
+    for (int k = 0; k < RC::XW; ++k) r[k] = st.x[k];
+    r[RC::B2_V] = V;
+    store_rec<RC::B2>(a.rec_b2, s, r);
+    a.Vs[s] = V;
+    if (a.V_out) a.V_out[a.c.perm[s]] = V;
+  }
+};
+
+// ===========================================================================
+// b2: moments over G(i) (V_j held fixed), in reduced form
+//   m0 = sum V W, m1 = sum V x W, m2 = sum V x x W,
+//   S0 = sum V g x, S2 = sum V g x x, S3 = sum V g x x x   (g = W'/r)
+// from which grad m0 = S0, d_g m1^a = S2^{ag} + delta_ag m0,
+// d_g m2^{ab} = S3^{abg} + delta_ag m1^b + delta_bg m1^a.
+// Then A, B, grad A, grad B from the reproducing conditions (Eq. RK).
+// ===========================================================================
+template <class R> struct PassB2 {
+  static constexpr bool GATHER = true;
+  static constexpr int QUEUE = Q_B2;
+  using RC = Rec<R>;
+  struct Args {
+    Common c;
+    const R* __restrict__ rec_b2;
+    const R* __restrict__ hs;
+    R* coef;      // [n][16] sorted, AoS
+    R* mom;       // [n][kMomW] sorted, AoS
+    R* coef_out;  // [16][n] caller order (optional)
+  };
+  struct State {
+    R x[RC::XW];
+    R ih, L, halfL, V;
+    Acc<R> m0;
+    R m1[3], m2[6], S0[3], S2[6], S3[10];
+  };
+  __device__ static void begin(const Args& a, int64_t s, State& st) {
+    R r[RC::B2];
+    load_rec<RC::B2>(a.rec_b2, s, r);
+#pragma unroll
+    for (int k = 0; k < RC::XW; ++k) st.x[k] = r[k];
+    st.V = r[RC::B2_V];
+    st.ih = R(1) / a.hs[s];
+    double L = a.c.box_L[a.c.boxid[s]];
+    st.L = (R)L;
+    st.halfL = (R)(0.5 * L);
+    st.m0 = Acc<R>();
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { st.m1[k] = R(0); st.S0[k] = R(0); }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { st.m2[k] = R(0); st.S2[k] = R(0); }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) st.S3[k] = R(0);
+  }
+  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
+    R r[RC::B2];
+    load_rec<RC::B2>(a.rec_b2, j, r);
+    R d[3];
+    separation(st.x, r, st.L, st.halfL, d);
+    R W, g;
+    wendland(radius(dot3(d, d)), st.ih, W, g);
+    const R Vj = r[RC::B2_V];
+    const R w = Vj * W, gv = Vj * g;
+    st.m0.add(w);
+    const R xx[6] = {d[0] * d[0], d[0] * d[1], d[0] * d[2], d[1] * d[1], d[1] * d[2], d[2] * d[2]};
+    const R xxx[10] = {xx[0] * d[0], xx[0] * d[1], xx[0] * d[2], xx[1] * d[1], xx[1] * d[2],
+                       xx[2] * d[2], xx[3] * d[1], xx[3] * d[2], xx[4] * d[2], xx[5] * d[2]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { st.m1[k] += w * d[k]; st.S0[k] += gv * d[k]; }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { st.m2[k] += w * xx[k]; st.S2[k] += gv * xx[k]; }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) st.S3[k] += gv * xxx[k];
+  }
+  __device__ static void end(const Args& a, int64_t s, State& st) {
+    st.m0.add(st.V * wendland0(st.ih));
+    R mom[kMomW];
+    mom[0] = st.m0.s;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { mom[1 + k] = st.m1[k]; mom[10 + k] = st.S0[k]; }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { mom[4 + k] = st.m2[k]; mom[13 + k] = st.S2[k]; }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) mom[19 + k] = st.S3[k];
+    mom[29] = mom[30] = mom[31] = R(0);
+    store_rec<kMomW>(a.mom, s, mom);
+    R C[16];
+    bool sing = rk_coefficients<R>(mom, C);
+    if (sing) {
+      atomicAdd(&a.c.hdr->nsingular, 1ull);
+      set_status(a.c.hdr, CRK_ESINGULAR);
+    }
+    store_rec<16>(a.coef, s, C);
+    if (a.coef_out) {
+      const int64_t p = a.c.perm[s];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) a.coef_out[k * a.c.n + p] = C[k];
+    }
+  }
+
+};
+
+// ===========================================================================
+// prologue of crk_rates: pack (x, V, m, v) records, sorted u
+// ===========================================================================
+template <class R>
+__global__ void k_pack_c1(const R* __restrict__ xs, const R* __restrict__ Vs,
+                          const R* __restrict__ ms, const R* __restrict__ v,
+                          const R* __restrict__ u, const int32_t* __restrict__ perm, int64_t n,
+                          R* __restrict__ rec, R* __restrict__ us) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  using RC = Rec<R>;
+  R r[RC::C1];
+#pragma unroll
+  for (int k = 0; k < RC::C1; ++k) r[k] = R(0);
+  get_x(xs, n, s, r);
+  const int64_t p = perm[s];
+  r[RC::C1_V] = Vs[s];
+  r[RC::C1_M] = ms[s];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r[RC::C1_VEL + k] = v[k * n + p];
+  us[s] = u[p];
+  store_rec<RC::C1>(rec, s, r);
+}
+
+// ===========================================================================
+// c1: density (Eq. rhow, gas only) and velocity gradient (Eq. gradv) over
+// G(i), then EOS, sound speed and the relaxation flag (App. A.1)
+// ===========================================================================
+template <class R> struct PassC1 {
+  static constexpr bool GATHER = true;
+  static constexpr int QUEUE = Q_C1;
+  using RC = Rec<R>;
+  struct Args {
+    Common c;
+    const R* __restrict__ rec_c1;
+    const R* __restrict__ hs;
+    const R* __restrict__ coef;
+    const R* __restrict__ us;
+    R* rec_c2;
+    R* rhos;   // sorted rho (adjoint)
+    R* Ds;     // sorted density denominator sum V_j^2 W^R_ij (adjoint)
+    R* rho_out;
+    R* gradv_out;
+    R gm1, ggm1, Cl, Cq, relax_dt;
+  };
+  struct State {
+    R x[RC::XW];
+    R ih, L, halfL, V, m, v[3];
+    R C[16];
+    Acc<R> num, den;
+    R gv[9];
+  };
+  __device__ static void begin(const Args& a, int64_t s, State& st) {
+    R r[RC::C1];
+    load_rec<RC::C1>(a.rec_c1, s, r);
+#pragma unroll
+    for (int k = 0; k < RC::XW; ++k) st.x[k] = r[k];
+    st.V = r[RC::C1_V];
+    st.m = r[RC::C1_M];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) st.v[k] = r[RC::C1_VEL + k];
+    load_rec<16>(a.coef, s, st.C);
+    st.ih = R(1) / a.hs[s];
+    double L = a.c.box_L[a.c.boxid[s]];
+    st.L = (R)L;
+    st.halfL = (R)(0.5 * L);
+    st.num = Acc<R>();
+    st.den = Acc<R>();
+#pragma unroll
+    for (int k = 0; k < 9; ++k) st.gv[k] = R(0);
+  }
+  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
+    R r[RC::C1];
+    load_rec<RC::C1>(a.rec_c1, j, r);
+    R d[3];
+    separation(st.x, r, st.L, st.halfL, d);
+    R W, g;
+    wendland(radius(dot3(d, d)), st.ih, W, g);
+    const R Vj = r[RC::C1_V];
+    const R WR = st.C[0] * (R(1) + (st.C[1] * d[0] + st.C[2] * d[1] + st.C[3] * d[2])) * W;
+    R G[3];
+    rk_gradient(st.C, d, W, g, true, G);
+    st.num.add(r[RC::C1_M] * Vj * WR);
+    st.den.add(Vj * Vj * WR);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const R t = Vj * (st.v[p] - r[RC::C1_VEL + p]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) st.gv[3 * p + q] -= t * G[q];
+    }
+  }
+  __device__ static void end(const Args& a, int64_t s, State& st) {
+    const R WR0 = st.C[0] * wendland0(st.ih);
+    st.num.add(st.m * st.V * WR0);
+    st.den.add(st.V * st.V * WR0);
+    const R rho = st.num.s / st.den.s;
+    const R u = a.us[s];
+    const R P = a.gm1 * rho * u;
+    const R cs = sqrt_(a.ggm1 * u);
+    const R div = st.gv[0] + st.gv[4] + st.gv[8];
+    const bool flag = a.relax_dt > R(0) && exp_(fabs(div) * a.relax_dt) > R(8);
+    R r[RC::C2];
+#pragma unroll
+    for (int k = 0; k < RC::C2; ++k) r[k] = R(0);
+#pragma unroll
+    for (int k = 0; k < RC::XW; ++k) r[k] = st.x[k];
+    r[RC::C2_IH] = st.ih;
+    r[RC::C2_V] = st.V;
+    r[RC::C2_P] = P;
+    r[RC::C2_QA] = a.Cl * rho * cs;
+    r[RC::C2_QB] = a.Cq * rho;
+    r[RC::C2_FLAG] = flag ? R(1) : R(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[RC::C2_VEL + k] = st.v[k];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) r[RC::C2_A + k] = st.C[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) r[RC::C2_GV + k] = st.gv[k];
+    store_rec<RC::C2>(a.rec_c2, s, r);
+    a.rhos[s] = rho;
+    a.Ds[s] = st.den.s;
+    const int64_t p = a.c.perm[s];
+    if (a.rho_out) a.rho_out[p] = rho;
+    if (a.gradv_out) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a.gradv_out[k * a.c.n + p] = st.gv[k];
+    }
+  }
+};
+
+// ===========================================================================
+// c2: pair rates over U(i) with the limited artificial viscosity
+//   Pi = P_i + P_j + Q_ij + Q_ji,   F_ij = -(1/2) V_i V_j Pi (G_ij - G_ji)
+//   dv_i/dt = sum F_ij / m_i,  du_i/dt = sum (1/2) F_ij.(v_j - v_i) / m_i
+// Every operand that appears for both members of a pair is formed by the same
+// expression on both sides, so F_ji = -F_ij bit for bit.
+// ===========================================================================
+template <class R> struct PassC2 {
+  static constexpr bool GATHER = false;
+  static constexpr int QUEUE = Q_C2;
+  using RC = Rec<R>;
+  struct Args {
+    Common c;
+    const R* __restrict__ rec_c2;
+    const R* __restrict__ ms;
+    R* dvdt;
+    R* dudt;
+    AVParams av;
+  };
+  struct State {
+    R ri[RC::C2];
+    R L, halfL;
+    R a[3];
+    Acc<R> e;
+  };
+  __device__ static void begin(const Args& a, int64_t s, State& st) {
+    load_rec<RC::C2>(a.rec_c2, s, st.ri);
+    double L = a.c.box_L[a.c.boxid[s]];
+    st.L = (R)L;
+    st.halfL = (R)(0.5 * L);
+    st.a[0] = st.a[1] = st.a[2] = R(0);
+    st.e = Acc<R>();
+  }
+  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
+    R rj[RC::C2];
+    load_rec<RC::C2>(a.rec_c2, j, rj);
+    R d[3];
+    separation(st.ri, rj, st.L, st.halfL, d);
+    const R r2 = dot3(d, d);
+    R F[3];
+    PairC2<R>::force(st.ri, rj, d, r2, a.av, F);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) st.a[p] += F[p];
+    const R* vi = st.ri + RC::C2_VEL;
+    const R* vj = rj + RC::C2_VEL;
+    st.e.add(R(-0.5) * (F[0] * (vi[0] - vj[0]) + F[1] * (vi[1] - vj[1]) + F[2] * (vi[2] - vj[2])));
+  }
+  __device__ static void end(const Args& a, int64_t s, State& st) {
+    const R im = R(1) / a.ms[s];
+    const int64_t p = a.c.perm[s];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a.dvdt[k * a.c.n + p] = st.a[k] * im;
+    a.dudt[p] = st.e.s * im;
+  }
+};
+
+// ===========================================================================
+// launch helpers and host drivers
+// ===========================================================================
+int sweep_grid(const Plan* plan, const void* kernel, int block, int which) {
+  int per_sm = plan->p.blocks_per_sm;
+  if (per_sm <= 0) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0);
+    per_sm = occ > 0 ? occ : 1;
+  }
+  (void)which;
+  int64_t need = (plan->ly.nw * 32 + block - 1) / block;
+  int64_t g = (int64_t)plan->num_sms * per_sm;
+  if (g > need) g = need;
+  return (int)(g > 0 ? g : 1);
+}
+
+template <class R>
+crk_status moments_impl(Plan* plan, cudaStream_t st, char* ws, const R* m, R* V_out, R* coef_out) {
+  const Layout& Ly = plan->ly;
+  const int64_t n = Ly.n;
+  Common c = make_common(plan, ws);
+  cudaMemsetAsync(&c.hdr->queue[Q_B1], 0, 2 * sizeof(int32_t), st);
+  if (n == 0) return CRK_OK;
+  R* rec_b1 = reinterpret_cast<R*>(ws + Ly.rec_b1);
+  R* rec_b2 = reinterpret_cast<R*>(ws + Ly.rec_b2);
+  R* ms = reinterpret_cast<R*>(ws + Ly.ms);
+  const R* xs = reinterpret_cast<const R*>(ws + Ly.xs);
+  const R* hs = reinterpret_cast<const R*>(ws + Ly.hs);
+  {
+    Phase ph(plan, st, "pack_b1", 1);
+    k_pack_b1<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xs, m, c.perm, n, rec_b1, ms);
+  }
+  typename PassB1<R>::Args a1{c, rec_b1, hs, rec_b2, reinterpret_cast<R*>(ws + Ly.Vs), V_out};
+  launch_sweep<PassB1<R>>(plan, st, a1, "b1_volume");
+  typename PassB2<R>::Args a2{c, rec_b2, hs, reinterpret_cast<R*>(ws + Ly.coef),
+                              reinterpret_cast<R*>(ws + Ly.mom), coef_out};
+  launch_sweep<PassB2<R>>(plan, st, a2, "b2_moments");
+  return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
+}
+
+template <class R>
+crk_status rates_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u, R* dvdt,
+                      R* dudt, R* rho_out, R* gradv_out) {
+  const Layout& Ly = plan->ly;
+  const int64_t n = Ly.n;
+  const crk_params& p = plan->p;
+  Common c = make_common(plan, ws);
+  cudaMemsetAsync(&c.hdr->queue[Q_C1], 0, 2 * sizeof(int32_t), st);
+  if (n == 0) return CRK_OK;
+  R* rec_c1 = reinterpret_cast<R*>(ws + Ly.rec_c1);
+  R* rec_c2 = reinterpret_cast<R*>(ws + Ly.rec_c2);
+  R* us = reinterpret_cast<R*>(ws + Ly.us);
+  {
+    Phase ph(plan, st, "pack_c1", 1);
+    k_pack_c1<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        reinterpret_cast<const R*>(ws + Ly.xs), reinterpret_cast<const R*>(ws + Ly.Vs),
+        reinterpret_cast<const R*>(ws + Ly.ms), v, u, c.perm, n, rec_c1, us);
+  }
+  typename PassC1<R>::Args a1{c,
+                              rec_c1,
+                              reinterpret_cast<const R*>(ws + Ly.hs),
+                              reinterpret_cast<const R*>(ws + Ly.coef),
+                              us,
+                              rec_c2,
+                              reinterpret_cast<R*>(ws + Ly.rhos),
+                              reinterpret_cast<R*>(ws + Ly.Ds),
+                              rho_out,
+                              gradv_out,
+                              (R)(p.gamma - 1.0),
+                              (R)(p.gamma * (p.gamma - 1.0)),
+                              (R)p.Cl,
+                              (R)p.Cq,
+                              (R)p.relax_dt};
+  launch_sweep<PassC1<R>>(plan, st, a1, "c1_density");
+  typename PassC2<R>::Args a2{c, rec_c2, reinterpret_cast<const R*>(ws + Ly.ms), dvdt, dudt,
+                              AVParams{p.eta_crit, p.eta_fold, p.eps2, p.limiter}};
+  launch_sweep<PassC2<R>>(plan, st, a2, "c2_rates");
+  return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
+}
+
+// Per-particle forward state (V, coefficients, density, velocity gradient and
+// the rate records) for the adjoint, from the masses packed by the last
+// crk_moments and the given v, u.
+template <class R>
+crk_status forward_state_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u) {
+  const Layout& Ly = plan->ly;
+  const int64_t n = Ly.n;
+  const crk_params& p = plan->p;
+  Common c = make_common(plan, ws);
+  cudaMemsetAsync(&c.hdr->queue[Q_B1], 0, 4 * sizeof(int32_t), st);
+  if (n == 0) return CRK_OK;
+  const R* hs = reinterpret_cast<const R*>(ws + Ly.hs);
+  R* rec_b2 = reinterpret_cast<R*>(ws + Ly.rec_b2);
+  typename PassB1<R>::Args a1{c, reinterpret_cast<const R*>(ws + Ly.rec_b1), hs, rec_b2,
+                              reinterpret_cast<R*>(ws + Ly.Vs), nullptr};
+  launch_sweep<PassB1<R>>(plan, st, a1, "b1_volume");
+  typename PassB2<R>::Args a2{c, rec_b2, hs, reinterpret_cast<R*>(ws + Ly.coef),
+                              reinterpret_cast<R*>(ws + Ly.mom), nullptr};
+  launch_sweep<PassB2<R>>(plan, st, a2, "b2_moments");
+  R* rec_c1 = reinterpret_cast<R*>(ws + Ly.rec_c1);
+  R* us = reinterpret_cast<R*>(ws + Ly.us);
+  {
+    Phase ph(plan, st, "pack_c1", 1);
+    k_pack_c1<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        reinterpret_cast<const R*>(ws + Ly.xs), reinterpret_cast<const R*>(ws + Ly.Vs),
+        reinterpret_cast<const R*>(ws + Ly.ms), v, u, c.perm, n, rec_c1, us);
+  }
+  typename PassC1<R>::Args a3{c, rec_c1, hs, reinterpret_cast<const R*>(ws + Ly.coef), us,
+                              reinterpret_cast<R*>(ws + Ly.rec_c2),
+                              reinterpret_cast<R*>(ws + Ly.rhos), reinterpret_cast<R*>(ws + Ly.Ds),
+                              nullptr, nullptr, (R)(p.gamma - 1.0),
+                              (R)(p.gamma * (p.gamma - 1.0)), (R)p.Cl, (R)p.Cq, (R)p.relax_dt};
+  launch_sweep<PassC1<R>>(plan, st, a3, "c1_density");
+  return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
+}
+template crk_status forward_state_impl<float>(Plan*, cudaStream_t, char*, const float*,
+                                              const float*);
+template crk_status forward_state_impl<double>(Plan*, cudaStream_t, char*, const double*,
+                                               const double*);
+
+template crk_status moments_impl<float>(Plan*, cudaStream_t, char*, const float*, float*, float*);
+template crk_status moments_impl<double>(Plan*, cudaStream_t, char*, const double*, double*,
+                                         double*);
+template crk_status rates_impl<float>(Plan*, cudaStream_t, char*, const float*, const float*,
+                                      float*, float*, float*, float*);
+template crk_status rates_impl<double>(Plan*, cudaStream_t, char*, const double*, const double*,
+                                       double*, double*, double*, double*);
+
+}  // namespace crk

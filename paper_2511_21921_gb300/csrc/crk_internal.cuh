@@ -1,0 +1,86 @@
+// crk_internal.cuh -- host-side plan and the functions each translation unit
+// provides to the C ABI layer.
+#pragma once
+
+#include <algorithm>
+#include <utility>
+
+#include "crk_common.cuh"
+
+struct crk_plan;
+
+namespace crk {
+
+struct Tuning {
+  int block_threads = 256;
+  int blocks_per_sm = 0;  // 0: occupancy-derived
+};
+
+struct Plan {
+  crk_params p{};
+  int64_t n_max = 0;
+  int32_t nb_max = 0;
+  int num_sms = 0;
+  int device = 0;
+  // state of the workspace built last
+  Layout ly{};
+  bool built = false;
+  bool has_moments = false;
+  bool has_rates = false;
+  bool sorted_keys_in_key0 = true;
+  const void* ws_built = nullptr;
+  int64_t n = 0;
+  int32_t nb = 0;
+  Tuning tune[16];
+  // instrumentation
+  long long launches = 0;
+  bool timing = false;
+  static constexpr int kMaxTimed = 256;
+  cudaEvent_t ev[2 * kMaxTimed] = {};
+  const char* ev_name[kMaxTimed] = {};
+  int n_timed = 0;
+  bool ev_ready = false;
+};
+
+// Bracket one phase with timing events (when enabled) and count its kernels.
+struct Phase {
+  Plan* p;
+  cudaStream_t st;
+  int slot = -1;
+  Phase(Plan* plan, cudaStream_t s, const char* name, int kernels);
+  void end();  // record the stop event now (idempotent)
+  ~Phase() { end(); }
+};
+
+Layout make_layout(const crk_params& p, int64_t n, int32_t nb);
+
+template <class T>
+void exclusive_scan(const T* in, T* out, int64_t n, void* tmp, T* total_out, cudaStream_t st);
+
+template <class R>
+crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int32_t nb,
+                           const int64_t* box_off, const double* box_L, const double* x,
+                           const R* h);
+crk_status neighbors_csr_impl(Plan* plan, cudaStream_t st, char* ws, int32_t mode,
+                              int64_t* row_ptr, int32_t* col, int64_t cap, int64_t* nnz);
+
+template <class R>
+crk_status moments_impl(Plan* plan, cudaStream_t st, char* ws, const R* m, R* V_out, R* coef_out);
+template <class R>
+crk_status rates_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u, R* dvdt,
+                      R* dudt, R* rho_out, R* gradv_out);
+template <class R>
+crk_status forward_state_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u);
+template <class R>
+crk_status adjoint_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u,
+                        const R* g_dvdt, const R* g_dudt, R* g_x, R* g_v, R* g_u, R* g_h,
+                        int recompute);
+
+// persistent grid size for a sweep kernel
+int sweep_grid(const Plan* plan, const void* kernel, int block, int which);
+
+}  // namespace crk
+
+struct crk_plan {
+  crk::Plan impl;
+};

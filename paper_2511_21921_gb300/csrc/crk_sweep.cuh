@@ -1,0 +1,288 @@
+// crk_sweep.cuh -- the persistent neighbor-sweep skeleton and the pair
+// arithmetic shared by the forward sweeps and their adjoints.
+#pragma once
+
+#include "crk_internal.cuh"
+
+namespace crk {
+
+struct Common {
+  DevHeader* hdr;
+  int64_t n, nw;
+  const uint32_t* __restrict__ ell;
+  const int64_t* __restrict__ woff;
+  const int32_t* __restrict__ cnt_g;
+  const int32_t* __restrict__ cnt_u;
+  const int32_t* __restrict__ wlen_g;
+  const int32_t* __restrict__ wlen_u;
+  const int32_t* __restrict__ boxid;
+  const double* __restrict__ box_L;
+  const int32_t* __restrict__ perm;
+  int64_t cap;
+};
+
+inline Common make_common(const Plan* plan, char* ws) {
+  const Layout& Ly = plan->ly;
+  Common c;
+  c.hdr = reinterpret_cast<DevHeader*>(ws + Ly.hdr);
+  c.n = Ly.n;
+  c.nw = Ly.nw;
+  c.ell = reinterpret_cast<const uint32_t*>(ws + Ly.ell);
+  c.woff = reinterpret_cast<const int64_t*>(ws + Ly.woff);
+  c.cnt_g = reinterpret_cast<const int32_t*>(ws + Ly.cnt_g);
+  c.cnt_u = reinterpret_cast<const int32_t*>(ws + Ly.cnt_u);
+  c.wlen_g = reinterpret_cast<const int32_t*>(ws + Ly.wlen_g);
+  c.wlen_u = reinterpret_cast<const int32_t*>(ws + Ly.wlen_u);
+  c.boxid = reinterpret_cast<const int32_t*>(ws + Ly.boxid);
+  c.box_L = reinterpret_cast<const double*>(ws + Ly.box_L);
+  c.perm = reinterpret_cast<const int32_t*>(ws + Ly.perm);
+  c.cap = Ly.cap;
+  return c;
+}
+
+// Persistent sweep: warps pull 32-particle work items from an atomic queue.
+template <class P>
+__global__ void __launch_bounds__(256) k_sweep(const typename P::Args a) {
+  const int lane = threadIdx.x & 31;
+  int32_t* q = &a.c.hdr->queue[P::QUEUE];
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(q, 1);
+    w = __shfl_sync(kFull, w, 0);
+    if (w >= a.c.nw) break;
+    const int64_t s = (int64_t)w * 32 + lane;
+    const bool live = s < a.c.n;
+    typename P::State st;
+    int len = 0;
+    if (live) {
+      P::begin(a, s, st);
+      len = P::GATHER ? a.c.cnt_g[s] : a.c.cnt_u[s];
+    }
+    int wl = P::GATHER ? a.c.wlen_g[w] : a.c.wlen_u[w];
+    const int64_t w0 = a.c.woff[w];
+    if (w0 + (int64_t)a.c.wlen_u[w] * 32 > a.c.cap) {  // lists overflowed at build time
+      wl = 0;
+      len = 0;
+      if (lane == 0) set_status(a.c.hdr, CRK_ENOMEM);
+    }
+    const uint32_t* col = a.c.ell + w0 + lane;
+    for (int k = 0; k < wl; ++k) {
+      const uint32_t e = __ldg(col + (int64_t)k * 32);
+      if (k < len) P::pair(a, st, e & kIdxMask, e);
+    }
+    if (live) P::end(a, s, st);
+  }
+}
+
+template <class R> __device__ __forceinline__ R dot3(const R* a, const R* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+__device__ __forceinline__ void get_x(const float* xs, int64_t n, int64_t s, float* o) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a) o[a] = xs[a * n + s];
+}
+__device__ __forceinline__ void get_x(const double* xs, int64_t n, int64_t s, double* o) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) o[a] = xs[a * n + s];
+}
+
+// Kahan-compensated accumulation (float only; plain in double)
+template <class R> struct Acc {
+  R s = R(0), c = R(0);
+  __device__ __forceinline__ void add(R v) {
+    if constexpr (sizeof(R) == 4) {
+      R y = v - c;
+      R t = s + y;
+      c = (t - s) - y;
+      s = t;
+    } else {
+      s += v;
+    }
+  }
+};
+
+constexpr int kMomW = 32;  // stored reduced moments per particle (29 used)
+
+// sym6 index of (a, b): xx, xy, xz, yy, yz, zz
+__device__ __forceinline__ int s6(int a, int b) {
+  return (a == 0) ? b : (b == 0 ? a : (a + b + 1));
+}
+// sym10 index of (a, b, c) in 000,001,002,011,012,022,111,112,122,222
+__device__ __forceinline__ int s10(int a, int b, int c) {
+  // sort a <= b <= c
+  int t;
+  if (a > b) { t = a; a = b; b = t; }
+  if (b > c) { t = b; b = c; c = t; }
+  if (a > b) { t = a; a = b; b = t; }
+  if (a == 0) return (b == 0) ? c : (b == 1 ? 2 + c : 5);
+  if (a == 1) return (b == 1) ? 5 + c : 8;
+  return 9;
+}
+
+// Coefficients from the reduced moments.  The 3x3 inverse of m2, B and A
+// are formed in double; the gradient terms in R.  Returns true when m2 is
+// singular (then A = 1 and everything else 0, the uncorrected kernel).
+template <class R>
+__device__ bool rk_coefficients(const R* mom, R* C) {
+  const double m0 = mom[0];
+  const double m1[3] = {mom[1], mom[2], mom[3]};
+  const double a = mom[4], b = mom[5], c = mom[6], d = mom[7], e = mom[8], f = mom[9];
+  const double c00 = d * f - e * e, c01 = c * e - b * f, c02 = b * e - c * d;
+  const double c11 = a * f - c * c, c12 = b * c - a * e, c22 = a * d - b * b;
+  const double det = a * c00 + b * c01 + c * c02;
+  const double tr = (fabs(a) + fabs(d) + fabs(f)) / 3.0;
+  if (!(fabs(det) > 1e-12 * tr * tr * tr)) {
+    C[0] = R(1);
+#pragma unroll
+    for (int k = 1; k < 16; ++k) C[k] = R(0);
+    return true;
+  }
+  const double id = 1.0 / det;
+  const double M[3][3] = {{c00 * id, c01 * id, c02 * id},
+                          {c01 * id, c11 * id, c12 * id},
+                          {c02 * id, c12 * id, c22 * id}};
+  double Mm1[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Mm1[i] = M[i][0] * m1[0] + M[i][1] * m1[1] + M[i][2] * m1[2];
+  const double A = 1.0 / (m0 - (m1[0] * Mm1[0] + m1[1] * Mm1[1] + m1[2] * Mm1[2]));
+  C[0] = (R)A;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) C[1 + i] = (R)(-Mm1[i]);
+  // gradients
+  const R Ar = (R)A;
+  R Mr[3][3], u[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    u[i] = (R)Mm1[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Mr[i][k] = (R)M[i][k];
+  }
+  const R m0r = mom[0];
+  const R* m1r = mom + 1;
+  const R* S0 = mom + 10;
+  const R* S2 = mom + 13;
+  const R* S3 = mom + 19;
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    R d1[3], t[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d1[i] = S2[s6(i, g)] + (i == g ? m0r : R(0));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R acc = R(0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        R d2 = S3[s10(i, k, g)] + (i == g ? m1r[k] : R(0)) + (k == g ? m1r[i] : R(0));
+        acc += d2 * u[k];
+      }
+      t[i] = acc;
+    }
+    const R sdot = S0[g] - R(2) * (u[0] * d1[0] + u[1] * d1[1] + u[2] * d1[2]) +
+                   (u[0] * t[0] + u[1] * t[1] + u[2] * t[2]);
+    C[4 + g] = -Ar * Ar * sdot;
+    const R w[3] = {t[0] - d1[0], t[1] - d1[1], t[2] - d1[2]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) C[7 + g * 3 + i] = Mr[i][0] * w[0] + Mr[i][1] * w[1] + Mr[i][2] * w[2];
+  }
+  return false;
+}
+
+// Corrected-kernel gradient for one side of a pair: the particle's own
+// coefficients C (A, B, gradA, gradB), 1/h and separation x from it:
+//   grad W^R = gradA (1+B.x) W + A (gradB.x + B) W + A (1+B.x) g x
+// Written once so that G_ij seen from i and G_ij seen from j (as their G_ji)
+// round identically.
+template <class R>
+__device__ __forceinline__ void rk_gradient(const R* C, const R* x, R W, R g, bool rk, R* G) {
+  if (!rk) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[k] = g * x[k];
+    return;
+  }
+  const R A = C[0];
+  const R lin = R(1) + (C[1] * x[0] + C[2] * x[1] + C[3] * x[2]);
+  const R linW = lin * W, AW = A * W, Alg = A * (lin * g);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const R dBx = C[7 + 3 * k] * x[0] + C[8 + 3 * k] * x[1] + C[9 + 3 * k] * x[2];
+    G[k] = C[4 + k] * linW + AW * (dBx + C[1 + k]) + Alg * x[k];
+  }
+}
+
+struct AVParams {
+  double eta_crit, eta_fold, eps2;
+  int limiter;
+};
+
+// The shared pair kernel: returns F (force on i from j, = m_i a_ij) and the
+// intermediate quantities the adjoint needs.  xi/xj are the full c2 records.
+template <class R> struct PairC2 {
+  using RC = Rec<R>;
+  // limiter phi from a = x.gv_i.x, b = x.gv_j.x:  4ab/(a+b)^2 when ab > 0
+  __device__ static __forceinline__ R limiter_phi(R a, R b) {
+    const R ab = a * b;
+    if (!(ab > R(0))) return R(0);
+    const R sm = a + b;
+    return R(4) * ab / (sm * sm);
+  }
+  __device__ static __forceinline__ void force(const R* ri, const R* rj, const R* d, R r2,
+                                               const AVParams& av, R* F) {
+    const R r = radius(r2);
+    const bool rk = ri[RC::C2_FLAG] == R(0) && rj[RC::C2_FLAG] == R(0);
+    R Wi, gi, Wj, gj;
+    wendland(r, ri[RC::C2_IH], Wi, gi);
+    wendland(r, rj[RC::C2_IH], Wj, gj);
+    const R nd[3] = {-d[0], -d[1], -d[2]};
+    R Gi[3], Gj[3];
+    rk_gradient(ri + RC::C2_A, d, Wi, gi, rk, Gi);
+    rk_gradient(rj + RC::C2_A, nd, Wj, gj, rk, Gj);
+    // artificial viscosity
+    const R* gvi = ri + RC::C2_GV;
+    const R* gvj = rj + RC::C2_GV;
+    R gix[3], gjx[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      gix[p] = gvi[3 * p] * d[0] + gvi[3 * p + 1] * d[1] + gvi[3 * p + 2] * d[2];
+      gjx[p] = gvj[3 * p] * d[0] + gvj[3 * p + 1] * d[1] + gvj[3 * p + 2] * d[2];
+    }
+    R phi = R(0);
+    const R ihi = ri[RC::C2_IH], ihj = rj[RC::C2_IH];
+    if (av.limiter) {
+      const R pa = d[0] * gix[0] + d[1] * gix[1] + d[2] * gix[2];
+      const R pb = d[0] * gjx[0] + d[1] * gjx[1] + d[2] * gjx[2];
+      phi = limiter_phi(pa, pb);
+      const R eta = r * fmin(ihi, ihj);
+      if (eta < R(av.eta_crit)) {
+        const R z = (eta - R(av.eta_crit)) / R(av.eta_fold);
+        phi = phi * exp_(-(z * z));
+      }
+    }
+    const R hphi = R(0.5) * phi;
+    R vh[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+      vh[p] = (ri[RC::C2_VEL + p] - rj[RC::C2_VEL + p]) - hphi * (gix[p] + gjx[p]);
+    const R vx = vh[0] * d[0] + vh[1] * d[1] + vh[2] * d[2];
+    R mui = vx * ihi / (r2 * (ihi * ihi) + R(av.eps2));
+    R muj = vx * ihj / (r2 * (ihj * ihj) + R(av.eps2));
+    mui = mui < R(0) ? mui : R(0);
+    muj = muj < R(0) ? muj : R(0);
+    const R Qi = mui * (ri[RC::C2_QB] * mui - ri[RC::C2_QA]);
+    const R Qj = muj * (rj[RC::C2_QB] * muj - rj[RC::C2_QA]);
+    const R Pi = (ri[RC::C2_P] + rj[RC::C2_P]) + (Qi + Qj);
+    const R pre = R(-0.5) * (ri[RC::C2_V] * rj[RC::C2_V]) * Pi;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) F[p] = pre * (Gi[p] - Gj[p]);
+  }
+};
+
+template <class P>
+void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const char* name) {
+  const int block = plan->p.block_threads > 0 ? plan->p.block_threads : 256;
+  const int grid = sweep_grid(plan, (const void*)k_sweep<P>, block, P::QUEUE);
+  Phase ph(plan, st, name, 1);
+  k_sweep<P><<<grid, block, 0, st>>>(a);
+}
+
+}  // namespace crk
