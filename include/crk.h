@@ -77,7 +77,7 @@ typedef struct {
   double relax_dt;  /* relaxation time step (App. A.1); 0 turns relaxation off */
   int32_t limiter;  /* 1: velocity-gradient limiter on the viscosity; 0: off */
   int32_t precision;/* crk_precision */
-  int32_t nbr_cap;  /* neighbor-list slots per particle reserved in the workspace; 0 = 160 */
+  int32_t nbr_cap;  /* neighbor-list slots per particle reserved in the workspace; 0 = 192 */
   int32_t block_threads; /* threads per block of the pair sweeps; 0 = autotuned default */
   int32_t blocks_per_sm; /* resident blocks per SM for the persistent sweeps; 0 = default */
   int32_t reserved[3];
@@ -146,10 +146,12 @@ typedef struct {
   int64_t n, n_boxes;
   int64_t gather_pairs;   /* sum_i |G(i)| - n: ordered pairs j != i with r < h_i */
   int64_t union_pairs;    /* sum_i |U(i)| */
-  int64_t list_slots;     /* neighbor-list slots used (with per-warp padding) */
-  int64_t list_capacity;  /* slots available in the workspace */
+  int64_t list_slots;     /* longest per-particle union list found by the build */
+  int64_t list_capacity;  /* list slots reserved per particle (params.nbr_cap) */
   int64_t tree_nodes;
   int64_t launches;       /* kernels this plan has launched since it was created (host count) */
+  int64_t tree_tests;     /* tree nodes tested by the last list build (counting pass) */
+  int64_t bucket_tests;   /* candidate buckets (8 particles each) tested by that pass */
   int32_t status;         /* device status word (not cleared) */
   int32_t reserved;
 } crk_stats;

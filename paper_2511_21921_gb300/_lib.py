@@ -32,7 +32,8 @@ class crk_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_boxes", C.c_int64), ("gather_pairs", C.c_int64),
                 ("union_pairs", C.c_int64), ("list_slots", C.c_int64),
                 ("list_capacity", C.c_int64), ("tree_nodes", C.c_int64),
-                ("launches", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32)]
+                ("launches", C.c_int64), ("tree_tests", C.c_int64), ("bucket_tests", C.c_int64),
+                ("status", C.c_int32), ("reserved", C.c_int32)]
 
 
 class crk_kernel_time(C.Structure):

@@ -247,6 +247,7 @@ __global__ void k_adj_prep(const R* __restrict__ gdv, const R* __restrict__ gdu,
 // ===========================================================================
 template <class R> struct PassA2 {
   static constexpr bool GATHER = false;
+  static constexpr int BLOCK = 64;
   static constexpr int QUEUE = Q_A_C2;
   using RC = Rec<R>;
   using AR = ARec<R>;
@@ -261,7 +262,7 @@ template <class R> struct PassA2 {
     R* rec_a1;
     R* acc;
     R* cbar;
-    AVParams av;
+    AVParams<R> av;
     R Cl, Cq, gm1, ggm1;
   };
   struct State {
@@ -326,9 +327,9 @@ template <class R> struct PassA2 {
       pb = d[0] * gjx[0] + d[1] * gjx[1] + d[2] * gjx[2];
       phi0 = PairC2<R>::limiter_phi(pa, pb);
       phi = phi0;
-      if (eta < R(a.av.eta_crit)) {
+      if (eta < a.av.eta_crit) {
         dampon = true;
-        z = (eta - R(a.av.eta_crit)) / R(a.av.eta_fold);
+        z = (eta - a.av.eta_crit) / a.av.eta_fold;
         damp = exp_(-(z * z));
         phi = phi0 * damp;
       }
@@ -341,8 +342,8 @@ template <class R> struct PassA2 {
       vh[p] = vij[p] - hphi * (gix[p] + gjx[p]);
     }
     const R vx = vh[0] * d[0] + vh[1] * d[1] + vh[2] * d[2];
-    const R Di = r2 * (ihi * ihi) + R(a.av.eps2);
-    const R Dj = r2 * (ihj * ihj) + R(a.av.eps2);
+    const R Di = r2 * (ihi * ihi) + a.av.eps2;
+    const R Dj = r2 * (ihj * ihj) + a.av.eps2;
     const R tmi = vx * ihi / Di, tmj = vx * ihj / Dj;
     const R mui = tmi < R(0) ? tmi : R(0);
     const R muj = tmj < R(0) ? tmj : R(0);
@@ -410,7 +411,7 @@ template <class R> struct PassA2 {
         phi0b = phib * damp;
         const R dampb = phib * phi0;
         const R zb = dampb * (R(-2) * z * damp);
-        const R etab = zb / R(a.av.eta_fold);
+        const R etab = zb / a.av.eta_fold;
         rb += etab * ihmin;
         const bool own = (ihi < ihj) || (ihi == ihj && st.s < (int64_t)j);
         if (own) ihib += etab * r;
@@ -502,6 +503,7 @@ template <class R> struct PassA2 {
 // ===========================================================================
 template <class R> struct PassA1 {
   static constexpr bool GATHER = false;
+  static constexpr int BLOCK = 64;
   static constexpr int QUEUE = Q_A_C1;
   using AR = ARec<R>;
   struct Args {
@@ -658,6 +660,7 @@ template <class R> struct PassA1 {
 // ===========================================================================
 template <class R> struct PassAB2 {
   static constexpr bool GATHER = false;
+  static constexpr int BLOCK = 64;
   static constexpr int QUEUE = Q_A_B2;
   using AR = ARec<R>;
   struct Args {
@@ -798,6 +801,7 @@ template <class R> struct PassAB2 {
 // ===========================================================================
 template <class R> struct PassAB1 {
   static constexpr bool GATHER = false;
+  static constexpr int BLOCK = 64;
   static constexpr int QUEUE = Q_A_B1;
   using AR = ARec<R>;
   struct Args {
@@ -905,7 +909,7 @@ crk_status adjoint_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const
                               rec_a1,
                               acc,
                               cbar,
-                              AVParams{p.eta_crit, p.eta_fold, p.eps2, p.limiter},
+                              make_av<R>(p),
                               (R)p.Cl,
                               (R)p.Cq,
                               (R)(p.gamma - 1.0),

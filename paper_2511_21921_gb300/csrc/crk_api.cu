@@ -20,8 +20,8 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.ni = L.nbk > 1 ? L.nbk - 1 : 0;
   L.nt = L.ni + L.nbk;
   L.ntiles = (n + kSortTile - 1) / kSortTile;
-  const int64_t slots_pp = p.nbr_cap > 0 ? p.nbr_cap : 160;
-  L.cap = slots_pp * L.nw * 32;
+  L.cap_pp = p.nbr_cap > 0 ? p.nbr_cap : 192;
+  L.cap = L.cap_pp * L.nw * 32;
   const size_t R = p.precision == CRK_FP64 ? 8 : 4;
   const int XW = p.precision == CRK_FP64 ? Rec<double>::XW : Rec<float>::XW;
   const int B1 = p.precision == CRK_FP64 ? Rec<double>::B1 : Rec<float>::B1;
@@ -43,7 +43,7 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.val0 = take(4 * N);
   L.val1 = take(4 * N);
   L.hist = take(4 * 256 * (size_t)std::max<int64_t>(L.ntiles, 1));
-  int64_t scan_n = std::max<int64_t>({256 * L.ntiles, n + 1, L.nw + 1});
+  int64_t scan_n = std::max<int64_t>({256 * L.ntiles, n + 1});
   L.scan_tmp = take(scan_tmp_bytes(scan_n));
   L.perm = take(4 * N);
   L.boxid = take(4 * N);
@@ -58,10 +58,9 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.parent = take(4 * NT);
   L.visit = take(4 * NI);
   L.cnt_g = take(4 * N);
-  L.cnt_u = take(4 * N);
+  L.cnt_s = take(4 * N);
   L.wlen_g = take(4 * NW);
-  L.wlen_u = take(4 * NW);
-  L.woff = take(8 * (NW + 1));
+  L.wlen_s = take(4 * NW);
   L.ell = take(4 * (size_t)L.cap);
   L.rec_b1 = take(R * B1 * N);
   L.rec_b2 = take(R * B2 * N);
@@ -327,10 +326,12 @@ crk_status crk_stats_get(crk_plan* plan, crk_stream_t stream, void* ws, crk_stat
   out->n_boxes = P.nb;
   out->gather_pairs = (int64_t)h.gather_pairs;
   out->union_pairs = (int64_t)h.union_pairs;
-  out->list_slots = (int64_t)h.slots_needed;
-  out->list_capacity = P.ly.cap;
+  out->list_slots = (int64_t)h.max_list;
+  out->list_capacity = P.ly.cap_pp;
   out->tree_nodes = P.ly.nt;
   out->launches = P.launches;
+  out->tree_tests = (int64_t)h.nbr_nodes;
+  out->bucket_tests = (int64_t)h.nbr_buckets;
   out->status = h.status;
   return CRK_OK;
 }

@@ -404,153 +404,288 @@ __device__ __forceinline__ float norm2(const float* d) {
 __device__ __forceinline__ double sq(double a) { return __dmul_rn(a, a); }
 __device__ __forceinline__ float sq(float a) { return a * a; }
 
-template <class R, bool FILL>
-__global__ void __launch_bounds__(256) k_nbr(
-    const R* __restrict__ xs, const R* __restrict__ hs, const int32_t* __restrict__ boxid,
+// One warp per 32 consecutive sorted particles walks the tree once for the
+// whole group (separately for each box present in the group): nodes are
+// tested 32 at a time against the group's bounding box grown by
+// max(h over the group, h_max of the node); overlapping buckets are staged
+// 4 at a time (32 particles) in shared memory and every lane tests its own
+// particle against all 32 with the exact pair predicate.  Traversal order is
+// fixed, so the counting and the filling pass see the same entries.
+// Center, half extent and largest h of the lanes with `in` set (all lanes
+// take part in the shuffles).
+__device__ __forceinline__ void group_bounds(bool in, const float* p, float h, float* gc, float* ge,
+                                             float& hg) {
+  float lo[3], hi[3];
+  hg = in ? h : 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = in ? p[a] : 3.0e38f;
+    hi[a] = in ? p[a] : -3.0e38f;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fminf(lo[a], __shfl_xor_sync(kFull, lo[a], o));
+      hi[a] = fmaxf(hi[a], __shfl_xor_sync(kFull, hi[a], o));
+    }
+    hg = fmaxf(hg, __shfl_xor_sync(kFull, hg, o));
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gc[a] = 0.5f * (lo[a] + hi[a]);
+    ge[a] = 0.5f * (hi[a] - lo[a]);
+  }
+}
+
+constexpr int kNbrWarps = 4;
+constexpr int kNodeStack = 2048;
+
+template <class R>
+__global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
+    const uint64_t* __restrict__ keys, const R* __restrict__ xs, const R* __restrict__ hs,
+    const int32_t* __restrict__ boxid,
     const double* __restrict__ box_L, int64_t n, int64_t nbk, int64_t ni, int64_t nt,
     const float* __restrict__ aabb, const float* __restrict__ hmaxn,
     const int32_t* __restrict__ brange, const int32_t* __restrict__ child,
-    int32_t* __restrict__ cnt_g, int32_t* __restrict__ cnt_u, int32_t* __restrict__ wlen_g,
-    int32_t* __restrict__ wlen_u, const int64_t* __restrict__ woff, uint32_t* __restrict__ ell,
-    int64_t cap, DevHeader* hdr) {
-  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
+    int32_t* __restrict__ cnt_g, int32_t* __restrict__ cnt_s, int32_t* __restrict__ wlen_g,
+    int32_t* __restrict__ wlen_s, uint32_t* __restrict__ ell, int64_t cap_pp, DevHeader* hdr) {
+  constexpr int XW = Prec<R>::XW;
+  __shared__ int32_t stk[kNbrWarps][kNodeStack];
+  __shared__ int32_t cand[kNbrWarps][64];
+  __shared__ R sx[kNbrWarps][XW][32];
+  __shared__ R sh[kNbrWarps][32];
+  __shared__ int32_t sb[kNbrWarps][32];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kNbrWarps + wib;
+  const int64_t nw = (n + 31) / 32;
+  if (w >= nw) return;  // whole warp
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t s = w * 32 + lane;
   const bool live = s < n;
-  int ng = 0, nu = 0;
-  int kg = 0, ks = 0;
-  int64_t wbase = 0;
+  R xi[XW];
+  R hi = R(0);
+  int32_t bi = -1;
+  float p[3] = {0.f, 0.f, 0.f};
   if (live) {
-    R xi[Prec<R>::XW];
     load_x(xs, n, s, xi);
-    const R hi = hs[s];
-    const R hi2 = sq(hi);
-    const int32_t bi = boxid[s];
-    const double Ld = box_L[bi];
-    const R L = (R)Ld, halfL = (R)(0.5 * Ld);
-    const float Lf = (float)Ld, halfLf = (float)(0.5 * Ld);
-    float p[3];
+    hi = hs[s];
+    bi = boxid[s];
 #pragma unroll
     for (int a = 0; a < 3; ++a) p[a] = (float)xpos(xs, n, s, a);
-    const float hif = (float)hi;
-    if (FILL) {
-      wbase = woff[s >> 5] + lane;
-      ks = cnt_g[s];
+  } else {
+#pragma unroll
+    for (int a = 0; a < XW; ++a) xi[a] = R(0);
+  }
+  const R hi2 = sq(hi);
+  // gather entries fill this lane's column from the front, scatter-only
+  // entries from the back; kg + ks > cap_pp means the column overflowed
+  int kg = 0, ks = 0;
+  const int64_t wbase = w * cap_pp * 32 + lane;
+  bool overflow = false;
+  unsigned long long cnt_nodes = 0, cnt_buckets = 0;
+  // Lane groups to traverse: one per box present in the warp, each split at
+  // its highest differing Morton bit when that shrinks the searched volume
+  // (32 consecutive keys can straddle a coarse octree boundary and then span
+  // much of the box).
+  const uint64_t mykey = live ? keys[s] : 0ull;
+  unsigned todo[8];
+  int ntodo = 0;
+  unsigned remaining = __ballot_sync(kFull, live);
+  while (remaining || ntodo) {
+    unsigned m;
+    if (ntodo == 0) {
+      const int l0 = __ffs(remaining) - 1;
+      const int32_t b0 = __shfl_sync(kFull, bi, l0);
+      m = __ballot_sync(kFull, live && bi == b0);
+      remaining &= ~m;
+    } else {
+      m = todo[--ntodo];
     }
-    int32_t stack[kStackDepth];
-    int sp = 0;
-    stack[sp++] = (ni > 0) ? 0 : (int32_t)ni;  // root (a lone bucket when ni == 0)
-    while (sp > 0) {
-      int32_t node = stack[--sp];
-      if (node >= ni) {
-        int64_t b = node - ni;
-        int64_t s0 = b * kBucket, s1 = min(n, s0 + kBucket);
-        for (int64_t j = s0; j < s1; ++j) {
-          if (j == s || boxid[j] != bi) continue;
-          R xj[Prec<R>::XW];
-          load_x(xs, n, j, xj);
-          R d[3];
-          separation(xi, xj, L, halfL, d);
-          R r2 = norm2(d);
-          R hj = hs[j];
-          bool g = r2 < hi2;
-          bool sc = r2 < sq(hj);
-          if (!(g || sc)) continue;
-          if (FILL) {
-            uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
-            int k = g ? kg++ : ks++;
-            int64_t slot = wbase + (int64_t)k * 32;
-            if (slot < cap) ell[slot] = e;
+    const bool act = (m >> lane) & 1u;
+    const int lead = __ffs(m) - 1;
+    const int32_t b = __shfl_sync(kFull, bi, lead);
+    const double Ld = box_L[b];
+    const R L = (R)Ld, halfL = (R)(0.5 * Ld);
+    const float Lf = (float)Ld, halfLf = (float)(0.5 * Ld);
+    float gc[3], ge[3], hg;
+    group_bounds(act, p, (float)hi, gc, ge, hg);
+    if (__popc(m) > 2 && ntodo <= 6) {
+      const uint64_t lk = __shfl_sync(kFull, mykey, lead);
+      uint64_t kx = act ? (mykey ^ lk) : 0ull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) kx |= __shfl_xor_sync(kFull, kx, o);
+      if (kx != 0ull) {
+        const int P = 63 - __clzll(kx);
+        const unsigned m1 = __ballot_sync(kFull, act && ((mykey >> P) & 1ull));
+        const unsigned m0 = m & ~m1;
+        float c0[3], e0[3], h0, c1[3], e1[3], h1;
+        group_bounds((m0 >> lane) & 1u, p, (float)hi, c0, e0, h0);
+        group_bounds((m1 >> lane) & 1u, p, (float)hi, c1, e1, h1);
+        const float V = (2.f * ge[0] + 2.f * hg) * (2.f * ge[1] + 2.f * hg) * (2.f * ge[2] + 2.f * hg);
+        const float V0 = (2.f * e0[0] + 2.f * h0) * (2.f * e0[1] + 2.f * h0) * (2.f * e0[2] + 2.f * h0);
+        const float V1 = (2.f * e1[0] + 2.f * h1) * (2.f * e1[1] + 2.f * h1) * (2.f * e1[2] + 2.f * h1);
+        if (m0 && m1 && V > 1.5f * (V0 + V1)) {
+          todo[ntodo++] = m1;
+          todo[ntodo++] = m0;
+          continue;
+        }
+      }
+    }
+    int sp = 0, nc = 0;
+    if (lane == 0) stk[wib][0] = (ni > 0) ? 0 : (int32_t)ni;
+    sp = 1;
+    __syncwarp();
+    while (sp > 0 || nc > 0) {
+      if (sp > 0) {
+        const int take = sp < 32 ? sp : 32;
+        const int32_t node = lane < take ? stk[wib][sp - take + lane] : -1;
+        sp -= take;
+        cnt_nodes += take;
+        __syncwarp();
+        bool ov = false;
+        if (node >= 0 && b >= brange[node] && b <= brange[nt + node]) {
+          float R_ = fmaxf(hg, hmaxn[node]) * 1.00001f + 1e-6f * Lf;
+          float g2 = 0.f;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float lo = aabb[a * nt + node], hi_ = aabb[(3 + a) * nt + node];
+            float dd = gc[a] - 0.5f * (lo + hi_);
+            if (dd > halfLf) dd -= Lf;
+            else if (dd < -halfLf) dd += Lf;
+            dd = fabsf(dd) - ge[a] - 0.5f * (hi_ - lo);
+            if (dd > 0.f) g2 += dd * dd;
+          }
+          ov = g2 <= R_ * R_;
+        }
+        const bool leaf = node >= ni;
+        const unsigned ml = __ballot_sync(kFull, ov && leaf);
+        const unsigned mi = __ballot_sync(kFull, ov && !leaf);
+        if (ov && leaf) cand[wib][nc + __popc(ml & lt)] = node - (int32_t)ni;
+        nc += __popc(ml);
+        const int npush = 2 * __popc(mi);
+        if (sp + npush > kNodeStack) {
+          overflow = true;
+          break;
+        }
+        if (ov && !leaf) {
+          const int at = sp + 2 * __popc(mi & lt);
+          stk[wib][at] = child[2 * node];
+          stk[wib][at + 1] = child[2 * node + 1];
+        }
+        sp += npush;
+        __syncwarp();
+      }
+      while (nc >= 4 || (sp == 0 && nc > 0)) {
+        const int take = nc < 4 ? nc : 4;
+        nc -= take;
+        cnt_buckets += take;
+        // stage the particles of buckets cand[nc .. nc+take)
+        {
+          const int kb = lane >> 3;
+          int64_t j = -1;
+          if (kb < take) {
+            const int64_t jj = (int64_t)cand[wib][nc + kb] * kBucket + (lane & 7);
+            if (jj < n) j = jj;
+          }
+          if (j >= 0) {
+            R t[XW];
+            load_x(xs, n, j, t);
+#pragma unroll
+            for (int a = 0; a < XW; ++a) sx[wib][a][lane] = t[a];
+            sh[wib][lane] = hs[j];
+            sb[wib][lane] = boxid[j];
           } else {
-            ng += g ? 1 : 0;
-            nu += 1;
+            sb[wib][lane] = -1;
           }
         }
-        continue;
-      }
-      // internal node: test both children, push the overlapping ones
+        __syncwarp();
+        if (act) {
+          const int64_t j0base = 0;
+          (void)j0base;
+#pragma unroll 4
+          for (int k = 0; k < 32; ++k) {
+            if (sb[wib][k] != b) continue;
+            const int64_t j = (int64_t)cand[wib][nc + (k >> 3)] * kBucket + (k & 7);
+            if (j == s) continue;
+            R xj[XW];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        int32_t ch = child[2 * node + c];
-        if (bi < brange[ch] || bi > brange[nt + ch]) continue;
-        float R_ = fmaxf(hif, hmaxn[ch]);
-        R_ = R_ * 1.00001f + 1e-6f * Lf;
-        float g2 = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          float lo = aabb[a * nt + ch], hi_ = aabb[(3 + a) * nt + ch];
-          float c_ = 0.5f * (lo + hi_), e = 0.5f * (hi_ - lo);
-          float dd = p[a] - c_;
-          if (dd > halfLf) dd -= Lf;
-          else if (dd < -halfLf) dd += Lf;
-          dd = fabsf(dd) - e;
-          if (dd > 0.f) g2 += dd * dd;
+            for (int a = 0; a < XW; ++a) xj[a] = sx[wib][a][k];
+            R d[3];
+            separation(xi, xj, L, halfL, d);
+            const R r2 = norm2(d);
+            const bool g = r2 < hi2;
+            const bool sc = r2 < sq(sh[wib][k]);
+            if (!(g || sc)) continue;
+            const uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
+            if (kg + ks < cap_pp) {
+              const int64_t k = g ? kg : cap_pp - 1 - ks;
+              ell[wbase + k * 32] = e;
+            }
+            if (g) ++kg; else ++ks;
+          }
         }
-        if (g2 <= R_ * R_) {
-          if (sp < kStackDepth) stack[sp++] = ch;
-          else set_status(hdr, CRK_ENOMEM);
-        }
+        __syncwarp();
       }
     }
+    if (overflow) break;
   }
-  if (!FILL) {
-    if (live) { cnt_g[s] = ng; cnt_u[s] = nu; }
-    int mg = ng, mu = nu;
-    unsigned long long sg = (unsigned long long)ng, su = (unsigned long long)nu;
+  if (overflow && lane == 0) set_status(hdr, CRK_ENOMEM);
+  const int need = kg + ks;
+  if (need > cap_pp) set_status(hdr, CRK_ENOMEM);
+  // counts that stay inside the column
+  const int cg = kg < cap_pp ? kg : (int)cap_pp;
+  const int cs = ks < cap_pp - cg ? ks : (int)(cap_pp - cg);
+  if (live) {
+    cnt_g[s] = cg;
+    cnt_s[s] = cs;
+  }
+  int mg = cg, ms = cs, mneed = need;
+  unsigned long long sg = (unsigned long long)kg, su = (unsigned long long)(kg + ks);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mg = max(mg, __shfl_xor_sync(kFull, mg, o));
-      mu = max(mu, __shfl_xor_sync(kFull, mu, o));
-      sg += __shfl_xor_sync(kFull, sg, o);
-      su += __shfl_xor_sync(kFull, su, o);
-    }
-    if (lane == 0 && (s - lane) < n) {
-      wlen_g[s >> 5] = mg;
-      wlen_u[s >> 5] = mu;
-      atomicAdd(&hdr->gather_pairs, sg);
-      atomicAdd(&hdr->union_pairs, su);
-    }
-  } else if (live) {
-    // pad this lane's column up to the warp's longest list
-    int wl = wlen_u[s >> 5];
-    for (int k = cnt_u[s]; k < wl; ++k) {
-      int64_t slot = wbase + (int64_t)k * 32;
-      if (slot < cap) ell[slot] = kSentinel;
-    }
+  for (int o = 16; o > 0; o >>= 1) {
+    mg = max(mg, __shfl_xor_sync(kFull, mg, o));
+    ms = max(ms, __shfl_xor_sync(kFull, ms, o));
+    mneed = max(mneed, __shfl_xor_sync(kFull, mneed, o));
+    sg += __shfl_xor_sync(kFull, sg, o);
+    su += __shfl_xor_sync(kFull, su, o);
   }
-}
-
-__global__ void k_slots(const int32_t* __restrict__ wlen_u, int64_t nw, int64_t* __restrict__ wslots) {
-  int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w < nw) wslots[w] = (int64_t)wlen_u[w] * 32;
-}
-
-__global__ void k_check_cap(const int64_t* __restrict__ total, int64_t cap, DevHeader* hdr) {
-  hdr->slots_needed = (unsigned long long)*total;
-  if (*total > cap) set_status(hdr, CRK_ENOMEM);
+  if (lane == 0) {
+    wlen_g[w] = mg;
+    wlen_s[w] = ms;
+    atomicAdd(&hdr->gather_pairs, sg);
+    atomicAdd(&hdr->union_pairs, su);
+    atomicMax(&hdr->max_list, (unsigned long long)mneed);
+    atomicAdd(&hdr->nbr_nodes, cnt_nodes);
+    atomicAdd(&hdr->nbr_buckets, cnt_buckets);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // neighbor sets as CSR in caller order (inspection / tests)
 // ---------------------------------------------------------------------------
-__global__ void k_csr_counts(const int32_t* __restrict__ perm, const int32_t* __restrict__ cnt,
-                             int64_t n, int64_t* __restrict__ rowcnt) {
+__global__ void k_csr_counts(const int32_t* __restrict__ perm, const int32_t* __restrict__ cg,
+                             const int32_t* __restrict__ cs, int mode, int64_t n,
+                             int64_t* __restrict__ rowcnt) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n) rowcnt[perm[s]] = cnt[s];
+  if (s < n) rowcnt[perm[s]] = cg[s] + (mode ? cs[s] : 0);
 }
 
-__global__ void k_csr_fill(const int32_t* __restrict__ perm, const int32_t* __restrict__ cnt,
-                           const int64_t* __restrict__ woff, const uint32_t* __restrict__ ell,
-                           int64_t n, const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
+__global__ void k_csr_fill(const int32_t* __restrict__ perm, const int32_t* __restrict__ cg,
+                           const int32_t* __restrict__ cs, int mode, int64_t cap_pp,
+                           const uint32_t* __restrict__ ell, int64_t n,
+                           const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
                            int64_t cap) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
-  int64_t p = perm[s];
-  int64_t r0 = row_ptr[p];
-  int c = cnt[s];
-  int64_t base = woff[s >> 5] + (s & 31);
-  for (int k = 0; k < c; ++k) {
-    uint32_t e = ell[base + (int64_t)k * 32];
-    int32_t j = perm[e & kIdxMask];
+  const int64_t p = perm[s];
+  const int64_t r0 = row_ptr[p];
+  const int ng = cg[s], ns = mode ? cs[s] : 0;
+  const int64_t base = (s >> 5) * cap_pp * 32 + (s & 31);
+  for (int k = 0; k < ng + ns; ++k) {
+    const int64_t slot = k < ng ? k : cap_pp - 1 - (k - ng);
+    const uint32_t e = ell[base + slot * 32];
+    const int32_t j = perm[e & kIdxMask];
     // insertion into the sorted prefix of this row
     int64_t pos = r0 + k;
     if (pos >= cap) return;
@@ -622,22 +757,17 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
                                                           hmaxn, brange);
   }
   ph_tree.end();
-  Phase ph_lists(plan, st, "build.lists", 7);
-  // neighbor lists: count, per-warp offsets, fill
+  Phase ph_lists(plan, st, "build.lists", 1);
+  // neighbor lists (one pass; fixed column of cap_pp slots per particle)
   int32_t* cnt_g = reinterpret_cast<int32_t*>(ws + Ly.cnt_g);
-  int32_t* cnt_u = reinterpret_cast<int32_t*>(ws + Ly.cnt_u);
+  int32_t* cnt_s = reinterpret_cast<int32_t*>(ws + Ly.cnt_s);
   int32_t* wlen_g = reinterpret_cast<int32_t*>(ws + Ly.wlen_g);
-  int32_t* wlen_u = reinterpret_cast<int32_t*>(ws + Ly.wlen_u);
-  int64_t* woff = reinterpret_cast<int64_t*>(ws + Ly.woff);
+  int32_t* wlen_s = reinterpret_cast<int32_t*>(ws + Ly.wlen_s);
   uint32_t* ell = reinterpret_cast<uint32_t*>(ws + Ly.ell);
-  const unsigned gw = (unsigned)((Ly.nw * 32 + 255) / 256);
-  k_nbr<R, false><<<gw, 256, 0, st>>>(xs, hs, boxid, wbox, n, nbk, ni, nt, aabb, hmaxn, brange,
-                                      child, cnt_g, cnt_u, wlen_g, wlen_u, woff, ell, Ly.cap, hdr);
-  k_slots<<<(unsigned)((Ly.nw + 255) / 256), 256, 0, st>>>(wlen_u, Ly.nw, woff);
-  exclusive_scan<int64_t>(woff, woff, Ly.nw, ws + Ly.scan_tmp, woff + Ly.nw, st);
-  k_check_cap<<<1, 1, 0, st>>>(woff + Ly.nw, Ly.cap, hdr);
-  k_nbr<R, true><<<gw, 256, 0, st>>>(xs, hs, boxid, wbox, n, nbk, ni, nt, aabb, hmaxn, brange,
-                                     child, cnt_g, cnt_u, wlen_g, wlen_u, woff, ell, Ly.cap, hdr);
+  const unsigned gw = (unsigned)((Ly.nw + kNbrWarps - 1) / kNbrWarps);
+  k_nbr<R><<<gw, kNbrWarps * 32, 0, st>>>(k0, xs, hs, boxid, wbox, n, nbk, ni, nt, aabb, hmaxn,
+                                          brange, child, cnt_g, cnt_s, wlen_g, wlen_s, ell,
+                                          Ly.cap_pp, hdr);
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }
 
@@ -653,8 +783,8 @@ crk_status neighbors_csr_impl(Plan* plan, cudaStream_t st, char* ws, int32_t mod
   const Layout& Ly = plan->ly;
   const int64_t n = Ly.n;
   const int32_t* perm = reinterpret_cast<const int32_t*>(ws + Ly.perm);
-  const int32_t* cnt = reinterpret_cast<const int32_t*>(ws + (mode == 0 ? Ly.cnt_g : Ly.cnt_u));
-  const int64_t* woff = reinterpret_cast<const int64_t*>(ws + Ly.woff);
+  const int32_t* cg = reinterpret_cast<const int32_t*>(ws + Ly.cnt_g);
+  const int32_t* cs = reinterpret_cast<const int32_t*>(ws + Ly.cnt_s);
   const uint32_t* ell = reinterpret_cast<const uint32_t*>(ws + Ly.ell);
   const unsigned g = (unsigned)((n + 255) / 256);
   {
@@ -662,15 +792,15 @@ crk_status neighbors_csr_impl(Plan* plan, cudaStream_t st, char* ws, int32_t mod
     if (cudaMemcpyAsync(&h, ws + Ly.hdr, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return CRK_ECUDA;
-    if ((int64_t)h.slots_needed > Ly.cap) return CRK_ENOMEM;
+    if ((int64_t)h.max_list > Ly.cap_pp) return CRK_ENOMEM;
   }
-  if (n > 0) k_csr_counts<<<g, 256, 0, st>>>(perm, cnt, n, row_ptr);
+  if (n > 0) k_csr_counts<<<g, 256, 0, st>>>(perm, cg, cs, mode, n, row_ptr);
   exclusive_scan<int64_t>(row_ptr, row_ptr, n, ws + Ly.scan_tmp, row_ptr + n, st);
   if (cudaMemcpyAsync(nnz, row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return CRK_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return CRK_ECUDA;
   if (*nnz > cap) return CRK_ENOMEM;
-  if (n > 0) k_csr_fill<<<g, 256, 0, st>>>(perm, cnt, woff, ell, n, row_ptr, col, cap);
+  if (n > 0) k_csr_fill<<<g, 256, 0, st>>>(perm, cg, cs, mode, Ly.cap_pp, ell, n, row_ptr, col, cap);
   if (cudaStreamSynchronize(st) != cudaSuccess) return CRK_ECUDA;
   return CRK_OK;
 }

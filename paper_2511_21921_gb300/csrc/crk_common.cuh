@@ -30,10 +30,12 @@ enum Queue {
 struct DevHeader {
   int32_t status;
   int32_t pad0;
-  unsigned long long slots_needed;
+  unsigned long long max_list;      // longest union list found by the build
   unsigned long long gather_pairs;
   unsigned long long union_pairs;
   unsigned long long nsingular;
+  unsigned long long nbr_nodes;    // tree nodes tested by the list build
+  unsigned long long nbr_buckets;  // candidate buckets staged by the list build
   int32_t queue[Q_N];
   int32_t pad1[16];
 };
@@ -188,14 +190,14 @@ template <class R> __device__ __forceinline__ R wendland0(R ih) {
 // host-side workspace layout
 // ---------------------------------------------------------------------------
 struct Layout {
-  int64_t n = 0, nb = 0, nw = 0, nbk = 0, ni = 0, nt = 0, ntiles = 0, cap = 0;
+  int64_t n = 0, nb = 0, nw = 0, nbk = 0, ni = 0, nt = 0, ntiles = 0, cap = 0, cap_pp = 0;
   int prec = 1;
   size_t total = 0;
   size_t hdr = 0, box_L = 0;
   size_t key0 = 0, key1 = 0, val0 = 0, val1 = 0, hist = 0, scan_tmp = 0;
   size_t perm = 0, boxid = 0, xs = 0, hs = 0, ms = 0, us = 0, vs = 0;
   size_t aabb = 0, hmaxn = 0, brange = 0, child = 0, parent = 0, visit = 0;
-  size_t cnt_g = 0, cnt_u = 0, wlen_g = 0, wlen_u = 0, woff = 0, ell = 0;
+  size_t cnt_g = 0, cnt_s = 0, wlen_g = 0, wlen_s = 0, ell = 0;
   size_t rec_b1 = 0, rec_b2 = 0, rec_c1 = 0, rec_c2 = 0, coef = 0, Vs = 0, rhos = 0;
   size_t gvs = 0, Ds = 0;
   // adjoint

@@ -32,6 +32,7 @@ __global__ void k_pack_b1(const R* __restrict__ xs, const R* __restrict__ m,
 // ===========================================================================
 template <class R> struct PassB1 {
   static constexpr bool GATHER = true;
+  static constexpr int BLOCK = 256;
   static constexpr int QUEUE = Q_B1;
   using RC = Rec<R>;
   struct Args {
@@ -92,6 +93,7 @@ template <class R> struct PassB1 {
 // ===========================================================================
 template <class R> struct PassB2 {
   static constexpr bool GATHER = true;
+  static constexpr int BLOCK = 256;
   static constexpr int QUEUE = Q_B2;
   using RC = Rec<R>;
   struct Args {
@@ -204,6 +206,7 @@ __global__ void k_pack_c1(const R* __restrict__ xs, const R* __restrict__ Vs,
 // ===========================================================================
 template <class R> struct PassC1 {
   static constexpr bool GATHER = true;
+  static constexpr int BLOCK = 256;
   static constexpr int QUEUE = Q_C1;
   using RC = Rec<R>;
   struct Args {
@@ -313,6 +316,7 @@ template <class R> struct PassC1 {
 // ===========================================================================
 template <class R> struct PassC2 {
   static constexpr bool GATHER = false;
+  static constexpr int BLOCK = 256;
   static constexpr int QUEUE = Q_C2;
   using RC = Rec<R>;
   struct Args {
@@ -321,7 +325,7 @@ template <class R> struct PassC2 {
     const R* __restrict__ ms;
     R* dvdt;
     R* dudt;
-    AVParams av;
+    AVParams<R> av;
   };
   struct State {
     R ri[RC::C2];
@@ -436,7 +440,7 @@ crk_status rates_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R
                               (R)p.relax_dt};
   launch_sweep<PassC1<R>>(plan, st, a1, "c1_density");
   typename PassC2<R>::Args a2{c, rec_c2, reinterpret_cast<const R*>(ws + Ly.ms), dvdt, dudt,
-                              AVParams{p.eta_crit, p.eta_fold, p.eps2, p.limiter}};
+                              make_av<R>(p)};
   launch_sweep<PassC2<R>>(plan, st, a2, "c2_rates");
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }

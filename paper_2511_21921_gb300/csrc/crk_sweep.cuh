@@ -10,15 +10,14 @@ struct Common {
   DevHeader* hdr;
   int64_t n, nw;
   const uint32_t* __restrict__ ell;
-  const int64_t* __restrict__ woff;
   const int32_t* __restrict__ cnt_g;
-  const int32_t* __restrict__ cnt_u;
+  const int32_t* __restrict__ cnt_s;
   const int32_t* __restrict__ wlen_g;
-  const int32_t* __restrict__ wlen_u;
+  const int32_t* __restrict__ wlen_s;
   const int32_t* __restrict__ boxid;
   const double* __restrict__ box_L;
   const int32_t* __restrict__ perm;
-  int64_t cap;
+  int64_t cap_pp;  // list slots per particle: gather part from the front, scatter-only from the back
 };
 
 inline Common make_common(const Plan* plan, char* ws) {
@@ -28,21 +27,20 @@ inline Common make_common(const Plan* plan, char* ws) {
   c.n = Ly.n;
   c.nw = Ly.nw;
   c.ell = reinterpret_cast<const uint32_t*>(ws + Ly.ell);
-  c.woff = reinterpret_cast<const int64_t*>(ws + Ly.woff);
   c.cnt_g = reinterpret_cast<const int32_t*>(ws + Ly.cnt_g);
-  c.cnt_u = reinterpret_cast<const int32_t*>(ws + Ly.cnt_u);
+  c.cnt_s = reinterpret_cast<const int32_t*>(ws + Ly.cnt_s);
   c.wlen_g = reinterpret_cast<const int32_t*>(ws + Ly.wlen_g);
-  c.wlen_u = reinterpret_cast<const int32_t*>(ws + Ly.wlen_u);
+  c.wlen_s = reinterpret_cast<const int32_t*>(ws + Ly.wlen_s);
   c.boxid = reinterpret_cast<const int32_t*>(ws + Ly.boxid);
   c.box_L = reinterpret_cast<const double*>(ws + Ly.box_L);
   c.perm = reinterpret_cast<const int32_t*>(ws + Ly.perm);
-  c.cap = Ly.cap;
+  c.cap_pp = Ly.cap_pp;
   return c;
 }
 
 // Persistent sweep: warps pull 32-particle work items from an atomic queue.
 template <class P>
-__global__ void __launch_bounds__(256) k_sweep(const typename P::Args a) {
+__global__ void __launch_bounds__(P::BLOCK) k_sweep(const typename P::Args a) {
   const int lane = threadIdx.x & 31;
   int32_t* q = &a.c.hdr->queue[P::QUEUE];
   for (;;) {
@@ -53,22 +51,23 @@ __global__ void __launch_bounds__(256) k_sweep(const typename P::Args a) {
     const int64_t s = (int64_t)w * 32 + lane;
     const bool live = s < a.c.n;
     typename P::State st;
-    int len = 0;
+    int lg = 0, ls = 0;
     if (live) {
       P::begin(a, s, st);
-      len = P::GATHER ? a.c.cnt_g[s] : a.c.cnt_u[s];
+      lg = a.c.cnt_g[s];
+      ls = P::GATHER ? 0 : a.c.cnt_s[s];
     }
-    int wl = P::GATHER ? a.c.wlen_g[w] : a.c.wlen_u[w];
-    const int64_t w0 = a.c.woff[w];
-    if (w0 + (int64_t)a.c.wlen_u[w] * 32 > a.c.cap) {  // lists overflowed at build time
-      wl = 0;
-      len = 0;
-      if (lane == 0) set_status(a.c.hdr, CRK_ENOMEM);
-    }
-    const uint32_t* col = a.c.ell + w0 + lane;
-    for (int k = 0; k < wl; ++k) {
+    const int wg = a.c.wlen_g[w];
+    const int wsct = P::GATHER ? 0 : a.c.wlen_s[w];
+    const uint32_t* col = a.c.ell + (int64_t)w * a.c.cap_pp * 32 + lane;
+    for (int k = 0; k < wg; ++k) {
       const uint32_t e = __ldg(col + (int64_t)k * 32);
-      if (k < len) P::pair(a, st, e & kIdxMask, e);
+      if (k < lg) P::pair(a, st, e & kIdxMask, e);
+    }
+    const uint32_t* back = col + (int64_t)(a.c.cap_pp - 1) * 32;
+    for (int k = 0; k < wsct; ++k) {
+      const uint32_t e = __ldg(back - (int64_t)k * 32);
+      if (k < ls) P::pair(a, st, e & kIdxMask, e);
     }
     if (live) P::end(a, s, st);
   }
@@ -210,10 +209,14 @@ __device__ __forceinline__ void rk_gradient(const R* C, const R* x, R W, R g, bo
   }
 }
 
-struct AVParams {
-  double eta_crit, eta_fold, eps2;
+// viscosity constants, converted once to the working precision
+template <class R> struct AVParams {
+  R eta_crit, eta_fold, eps2;
   int limiter;
 };
+template <class R> AVParams<R> make_av(const crk_params& p) {
+  return AVParams<R>{(R)p.eta_crit, (R)p.eta_fold, (R)p.eps2, p.limiter};
+}
 
 // The shared pair kernel: returns F (force on i from j, = m_i a_ij) and the
 // intermediate quantities the adjoint needs.  xi/xj are the full c2 records.
@@ -227,7 +230,7 @@ template <class R> struct PairC2 {
     return R(4) * ab / (sm * sm);
   }
   __device__ static __forceinline__ void force(const R* ri, const R* rj, const R* d, R r2,
-                                               const AVParams& av, R* F) {
+                                               const AVParams<R>& av, R* F) {
     const R r = radius(r2);
     const bool rk = ri[RC::C2_FLAG] == R(0) && rj[RC::C2_FLAG] == R(0);
     R Wi, gi, Wj, gj;
@@ -253,8 +256,8 @@ template <class R> struct PairC2 {
       const R pb = d[0] * gjx[0] + d[1] * gjx[1] + d[2] * gjx[2];
       phi = limiter_phi(pa, pb);
       const R eta = r * fmin(ihi, ihj);
-      if (eta < R(av.eta_crit)) {
-        const R z = (eta - R(av.eta_crit)) / R(av.eta_fold);
+      if (eta < av.eta_crit) {
+        const R z = (eta - av.eta_crit) / av.eta_fold;
         phi = phi * exp_(-(z * z));
       }
     }
@@ -264,8 +267,8 @@ template <class R> struct PairC2 {
     for (int p = 0; p < 3; ++p)
       vh[p] = (ri[RC::C2_VEL + p] - rj[RC::C2_VEL + p]) - hphi * (gix[p] + gjx[p]);
     const R vx = vh[0] * d[0] + vh[1] * d[1] + vh[2] * d[2];
-    R mui = vx * ihi / (r2 * (ihi * ihi) + R(av.eps2));
-    R muj = vx * ihj / (r2 * (ihj * ihj) + R(av.eps2));
+    R mui = vx * ihi / (r2 * (ihi * ihi) + av.eps2);
+    R muj = vx * ihj / (r2 * (ihj * ihj) + av.eps2);
     mui = mui < R(0) ? mui : R(0);
     muj = muj < R(0) ? muj : R(0);
     const R Qi = mui * (ri[RC::C2_QB] * mui - ri[RC::C2_QA]);
@@ -279,7 +282,7 @@ template <class R> struct PairC2 {
 
 template <class P>
 void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const char* name) {
-  const int block = plan->p.block_threads > 0 ? plan->p.block_threads : 256;
+  const int block = P::BLOCK;
   const int grid = sweep_grid(plan, (const void*)k_sweep<P>, block, P::QUEUE);
   Phase ph(plan, st, name, 1);
   k_sweep<P><<<grid, block, 0, st>>>(a);

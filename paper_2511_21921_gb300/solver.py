@@ -102,8 +102,7 @@ class Solver:
             st = L.crk_stats_get(self.plan, _stream(), ws)
             code = L.crk_status_poll(self.plan, _stream(), ws)
             if code == L.CRK_ENOMEM and st.list_slots > st.list_capacity:
-                per = math.ceil(st.list_slots / max(1, 32 * ((n + 31) // 32)) * 1.1) + 8
-                self._regrow(per)
+                self._regrow(int(math.ceil(st.list_slots * 1.05)) + 8)
                 continue
             L.check(code, "crk_cell_build (device)")
             return self

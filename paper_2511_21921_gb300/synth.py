@@ -139,11 +139,12 @@ def lognormal(n_side=64, sigma2=1.5, seed=1, kmin=90, kmax=110, L=1.0, h_cap=0.4
     return _finish(rng, x, h, L)
 
 
-def clumpy(n_side=128, n_clumps=200, sigma2=3.0, seed=2, kmin=90, kmax=110, L=1.0):
+def clumpy(n_side=128, n_clumps=200, sigma2=3.0, seed=2, kmin=90, kmax=110, L=1.0,
+           nc_min=1e3, nc_max=1e4):
     """Plummer clumps on a lognormal background (h spanning about two decades)."""
     rng = np.random.default_rng(seed)
     n = n_side ** 3
-    nc = np.round(np.exp(rng.uniform(np.log(1e3), np.log(1e4), size=n_clumps))).astype(np.int64)
+    nc = np.round(np.exp(rng.uniform(np.log(nc_min), np.log(nc_max), size=n_clumps))).astype(np.int64)
     contrast = 10.0 ** rng.uniform(2.0, 4.0, size=n_clumps)
     centers = rng.random((3, n_clumps)) * L
     parts = []

@@ -247,3 +247,34 @@ def test_call_order_enforced():
     s = Solver(100, 1, "mixed")
     rc = L.crk_rates(s.plan, None, 256, 0, 0, 0, 0)
     assert rc == L.CRK_ESTATE
+
+
+def test_list_capacity_overflow_regrows():
+    """A neighbor-list column too small for the longest list is reported on the
+    device (CRK_ENOMEM) and the Solver rebuilds with enough slots."""
+    d = synth.load("lognormal32")
+    n = d["h"].shape[0]
+    s = Solver(n, 1, "fp64", nbr_cap=24)
+    t = to_dev(d, "fp64")
+    s.cell_build(t["x"], t["h"], check=False)
+    assert s.poll() == L.CRK_ENOMEM
+    gpu, _ = run_forward(d, "fp64", solver=s)
+    assert s.params.nbr_cap > 24
+    ora = _oracle_all(d)
+    err = compare(gpu, ora)
+    assert err["dvdt"] < 1e-12 and err["dudt"] < 1e-12, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_clumpy_multiscale_parity(precision):
+    """Plummer clumps on a lognormal background (smoothing lengths spanning
+    about two decades): union sets differ strongly from gather sets."""
+    d = synth.clumpy(n_side=32, n_clumps=12, seed=31, nc_min=300, nc_max=1500)
+    gpu, s = run_forward(d, precision)
+    assert gpu["status"] == 0
+    ora = _oracle_all(d)
+    err = compare(gpu, ora)
+    tol = TOL[precision]
+    for k in ("dvdt", "dudt"):
+        assert err[k] < tol, (k, err)
+    assert d["h"].max() / d["h"].min() > 20
