@@ -4,14 +4,14 @@
  * 2511.21921) for gas particles in periodic boxes:
  *
  *   crk_cell_build  -- Morton sort, bucket tree and per-particle neighbor
- *                      lists (the paper's GPU tree with few rebuilds, Sec. 2.7).
+ *                      lists (the paper's GPU tree with few rebuilds, Sec. 2.9).
  *   crk_moments     -- gas volume V (App. A.2, Eq. Vg), geometric moments and
  *                      reproducing-kernel coefficients A, B, grad A, grad B
  *                      (App. A.1, Eq. RK; closed forms from the reproducing
  *                      conditions of the CRKSPH formulation the paper cites).
- *   crk_rates       -- RK density (Sec. 2.4.2, Eq. rhow, gas only), velocity
+ *   crk_rates       -- RK density (Sec. 2.5.1, Eq. rhow, gas only), velocity
  *                      gradient (App. A.1, Eq. gradv), ideal-gas EOS with
- *                      gamma from the parameters (5/3, Sec. 2.3), relaxation
+ *                      gamma from the parameters (5/3, Sec. 2.4.1), relaxation
  *                      flag (App. A.1), and pairwise momentum and compatible
  *                      energy rates with limited artificial viscosity (Sec. 2.1).
  *   crk_adjoint     -- vector-Jacobian product of the rates with respect to
@@ -69,7 +69,7 @@ typedef enum {
 } crk_precision;
 
 typedef struct {
-  double gamma;     /* adiabatic index; 5/3 for a monatomic ideal gas (Sec. 2.3) */
+  double gamma;     /* adiabatic index; 5/3 for a monatomic ideal gas (Sec. 2.4.1) */
   double Cl, Cq;    /* linear / quadratic artificial-viscosity coefficients */
   double eps2;      /* softening of the viscosity denominator |eta|^2 + eps2 */
   double eta_crit;  /* near-field damping applies when min(r/h_i, r/h_j) < eta_crit */

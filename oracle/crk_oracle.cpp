@@ -6,7 +6,7 @@
 //
 // What it computes (CRK-HACC, arXiv 2511.21921, and the CRKSPH formulation that
 // paper cites for the parts it does not print):
-//   * Wendland C4 kernel with compact support h (Sec. 2.1; App. A.2 footnote on
+//   * Wendland C4 kernel with compact support h (Sec. 2 preamble; App. A.2 footnote on
 //     the radius convention).
 //   * gas volume  V_i = m_i / sum_j m_j W(|x_ij|, h_i)            (App. A.2, Eq. Vg)
 //   * geometric moments m0, m1, m2 and their gradients, and the reproducing
@@ -14,10 +14,10 @@
 //     corrected kernel reproduces constant and linear fields   (App. A.1, Eq. RK;
 //     the paper defers the closed forms to the CRKSPH method paper)
 //   * corrected kernel W^R_ij = A_i (1 + B_i . x_ij) W_ij(h_i)    (App. A.1, Eq. RK)
-//   * gas density  rho_i = sum m_j V_j W^R_ij / sum V_j^2 W^R_ij  (Sec. 2.4.2, Eq. rhow,
+//   * gas density  rho_i = sum m_j V_j W^R_ij / sum V_j^2 W^R_ij  (Sec. 2.5.1, Eq. rhow,
 //     gas-only)
 //   * velocity gradient  grad v_i = -sum_j V_j (v_i - v_j) (x) grad W^R_ij (App. A.1, Eq. gradv)
-//   * ideal-gas EOS with gamma = 5/3                              (Sec. 2.3, EOS text)
+//   * ideal-gas EOS with gamma = 5/3                              (Sec. 2.4.1)
 //   * RK relaxation: exp(|div v_i| dt) > 8 => A=1, B=0 for any pair with that
 //     particle, applied symmetrically                            (App. A.1)
 //   * pairwise momentum and compatible-energy rates with a limited
@@ -243,7 +243,7 @@ template <class T> T kernel_g(T r, T h) {
 extern "C" {
 
 typedef struct {
-  double gamma;     // adiabatic index (5/3, Sec. 2.3)
+  double gamma;     // adiabatic index (5/3, Sec. 2.4.1)
   double Cl, Cq;    // linear and quadratic viscosity coefficients
   double eps2;      // softening of the viscosity denominator
   double eta_crit;  // near-field damping threshold on r/h

@@ -5,7 +5,7 @@
 //
 // The paper's solver keeps particles in tree leaves of a few hundred
 // particles and reuses that tree for hydro neighbor searches (Sec. 2.1,
-// App. A.4); its GPU tree is built to minimise rebuild cost (Sec. 2.7).  Here
+// App. A.4); its GPU tree is built to minimise rebuild cost (Sec. 2.9).  Here
 // the tree is a linear BVH over Morton-ordered buckets (one CUDA thread per
 // node, no spin waits), and its only job is to produce neighbor lists that
 // every later sweep reads without further distance tests.

@@ -24,7 +24,7 @@ def _params(**kw):
 
 # ---------------------------------------------------------------- kernel
 def test_wendland_normalised_by_quadrature():
-    """Wendland C4 with support h integrates to one over the ball (Sec. 2.1)."""
+    """Wendland C4 with support h integrates to one over the ball (Sec. 2 preamble)."""
     for h in (0.05, 0.3, 1.0):
         f = lambda r: 4 * np.pi * r * r * oracle.kernel(np.array([r]), h)[0][0]
         val, err = integrate.quad(f, 0.0, h, epsabs=1e-14, epsrel=1e-13, limit=200)
