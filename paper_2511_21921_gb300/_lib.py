@@ -65,7 +65,10 @@ _SIGS = {
     "crk_status_string": (C.c_char_p, [C.c_int]),
     "crk_timing_enable": (C.c_int, [_VP, C.c_int32]),
     "crk_timing_read": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_int32)]),
+    "crk_volume_static": (C.c_int, [_VP, C.c_int32, C.c_int64, C.c_double, C.c_double, _VP, _VP,
+                                    _VP, _VP]),
 }
+CRK_STATIC_MAX_PARTICLES = 65536
 
 _lib = None
 
@@ -182,3 +185,8 @@ def crk_timing_read(plan) -> list[tuple[str, float]]:
     cnt = C.c_int32()
     check(load().crk_timing_read(_VP(plan), buf, 256, C.byref(cnt)), "crk_timing_read")
     return [(buf[k].name.decode(), float(buf[k].ms)) for k in range(cnt.value)]
+
+
+def crk_volume_static(stream, precision, n, L, h_bound, x, h, m, V_out) -> int:
+    return load().crk_volume_static(_VP(stream), int(precision), int(n), float(L),
+                                    float(h_bound), _VP(x), _VP(h), _VP(m), _VP(V_out))
