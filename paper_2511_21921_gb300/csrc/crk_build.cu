@@ -455,7 +455,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
   __shared__ int32_t cand[kNbrWarps][64];
   __shared__ R sx[kNbrWarps][XW][32];
   __shared__ R sh[kNbrWarps][32];
-  __shared__ int32_t sb[kNbrWarps][32];
+  __shared__ float4 s4[kNbrWarps][32];
+  __shared__ int32_t sj[kNbrWarps][32];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kNbrWarps + wib;
   const int64_t nw = (n + 31) / 32;
@@ -510,6 +511,11 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
     const float Lf = (float)Ld, halfLf = (float)(0.5 * Ld);
     float gc[3], ge[3], hg;
     group_bounds(act, p, (float)hi, gc, ge, hg);
+    // nearest-image staging is exact for every pair in reach when the group
+    // extent plus the largest search radius stays below half the box
+    const float reach = fmaxf(hg, hmaxn[0]);
+    const bool fast = sizeof(R) == 4 &&
+                      2.f * fmaxf(ge[0], fmaxf(ge[1], ge[2])) + reach < 0.49f * Lf;
     if (__popc(m) > 2 && ntodo <= 6) {
       const uint64_t lk = __shfl_sync(kFull, mykey, lead);
       uint64_t kx = act ? (mykey ^ lk) : 0ull;
@@ -586,43 +592,77 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
           int64_t j = -1;
           if (kb < take) {
             const int64_t jj = (int64_t)cand[wib][nc + kb] * kBucket + (lane & 7);
-            if (jj < n) j = jj;
+            if (jj < n && boxid[jj] == b) j = jj;
           }
-          if (j >= 0) {
+          sj[wib][lane] = (int32_t)j;
+          if (fast) {
+            // float position moved to the periodic image nearest the group
+            // center; NaN for slots that hold no particle of this box
+            float4 t = make_float4(__int_as_float(0x7fffffff), 0.f, 0.f, __int_as_float(0x7fffffff));
+            if (j >= 0) {
+              float q[3];
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                q[a] = (float)xs[a * n + j];
+                const float dd = gc[a] - q[a];
+                q[a] += dd > halfLf ? Lf : (dd < -halfLf ? -Lf : 0.f);
+              }
+              const float hj = (float)hs[j];
+              t = make_float4(q[0], q[1], q[2], hj * hj);
+            }
+            s4[wib][lane] = t;
+          } else if (j >= 0) {
             R t[XW];
             load_x(xs, n, j, t);
 #pragma unroll
             for (int a = 0; a < XW; ++a) sx[wib][a][lane] = t[a];
             sh[wib][lane] = hs[j];
-            sb[wib][lane] = boxid[j];
-          } else {
-            sb[wib][lane] = -1;
           }
         }
         __syncwarp();
         if (act) {
-          const int64_t j0base = 0;
-          (void)j0base;
-#pragma unroll 4
-          for (int k = 0; k < 32; ++k) {
-            if (sb[wib][k] != b) continue;
-            const int64_t j = (int64_t)cand[wib][nc + (k >> 3)] * kBucket + (k & 7);
-            if (j == s) continue;
-            R xj[XW];
-#pragma unroll
-            for (int a = 0; a < XW; ++a) xj[a] = sx[wib][a][k];
-            R d[3];
-            separation(xi, xj, L, halfL, d);
-            const R r2 = norm2(d);
-            const bool g = r2 < hi2;
-            const bool sc = r2 < sq(sh[wib][k]);
-            if (!(g || sc)) continue;
-            const uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
-            if (kg + ks < cap_pp) {
-              const int64_t k = g ? kg : cap_pp - 1 - ks;
-              ell[wbase + k * 32] = e;
+          if (fast) {
+            // float predicate on the nearest images: no per-pair wrap
+            const float hi2f = (float)hi * (float)hi;
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+              const float4 t = s4[wib][k];
+              const float dx = p[0] - t.x, dy = p[1] - t.y, dz = p[2] - t.z;
+              const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+              const bool g = r2 < hi2f;
+              const bool sc = r2 < t.w;
+              if (!(g || sc)) continue;
+              const int32_t j = sj[wib][k];
+              if (j == s) continue;
+              const uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
+              if (kg + ks < cap_pp) {
+                const int64_t kk = g ? kg : cap_pp - 1 - ks;
+                ell[wbase + kk * 32] = e;
+              }
+              if (g) ++kg; else ++ks;
             }
-            if (g) ++kg; else ++ks;
+          } else {
+            // exact predicate (the oracle's, for the FP64 form)
+#pragma unroll 4
+            for (int k = 0; k < 32; ++k) {
+              const int32_t j = sj[wib][k];
+              if (j < 0 || j == s) continue;
+              R xj[XW];
+#pragma unroll
+              for (int a = 0; a < XW; ++a) xj[a] = sx[wib][a][k];
+              R d[3];
+              separation(xi, xj, L, halfL, d);
+              const R r2 = norm2(d);
+              const bool g = r2 < hi2;
+              const bool sc = r2 < sq(sh[wib][k]);
+              if (!(g || sc)) continue;
+              const uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
+              if (kg + ks < cap_pp) {
+                const int64_t kk = g ? kg : cap_pp - 1 - ks;
+                ell[wbase + kk * 32] = e;
+              }
+              if (g) ++kg; else ++ks;
+            }
           }
         }
         __syncwarp();

@@ -57,17 +57,27 @@ __global__ void __launch_bounds__(P::BLOCK) k_sweep(const typename P::Args a) {
       lg = a.c.cnt_g[s];
       ls = P::GATHER ? 0 : a.c.cnt_s[s];
     }
-    const int wg = a.c.wlen_g[w];
-    const int wsct = P::GATHER ? 0 : a.c.wlen_s[w];
     const uint32_t* col = a.c.ell + (int64_t)w * a.c.cap_pp * 32 + lane;
-    for (int k = 0; k < wg; ++k) {
-      const uint32_t e = __ldg(col + (int64_t)k * 32);
-      if (k < lg) P::pair(a, st, e & kIdxMask, e);
-    }
-    const uint32_t* back = col + (int64_t)(a.c.cap_pp - 1) * 32;
-    for (int k = 0; k < wsct; ++k) {
-      const uint32_t e = __ldg(back - (int64_t)k * 32);
-      if (k < ls) P::pair(a, st, e & kIdxMask, e);
+    if (P::GATHER) {
+      // gather part only: the same row of every lane is one 128-byte line
+      const int wg = a.c.wlen_g[w];
+      for (int k = 0; k < wg; ++k) {
+        const uint32_t e = __ldg(col + (int64_t)k * 32);
+        if (k < lg) P::pair(a, st, e & kIdxMask, e);
+      }
+    } else {
+      // gather part then scatter-only part as one list per lane, so the warp
+      // runs to its longest union list rather than to the sum of the longest
+      // parts
+      const int tot = lg + ls;
+      const int wmax = __reduce_max_sync(kFull, tot);
+      for (int k = 0; k < wmax; ++k) {
+        if (k < tot) {
+          const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
+          const uint32_t e = __ldg(col + slot * 32);
+          P::pair(a, st, e & kIdxMask, e);
+        }
+      }
     }
     if (live) P::end(a, s, st);
   }

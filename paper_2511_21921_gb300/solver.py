@@ -86,8 +86,14 @@ class Solver:
         assert x.dtype == torch.float64 and x.shape == (3, n) and x.is_contiguous()
         assert h.dtype == self.dtype and h.is_contiguous()
         if box_off is None:
-            box_off = torch.tensor([0, n], dtype=torch.int64, device=self.device)
-            box_L = torch.tensor([float(L_box)], dtype=torch.float64, device=self.device)
+            # single box: made once and reused (no host copy inside graph capture)
+            key = (n, float(L_box))
+            if getattr(self, "_box_key", None) != key:
+                self._box_default = (
+                    torch.tensor([0, n], dtype=torch.int64, device=self.device),
+                    torch.tensor([float(L_box)], dtype=torch.float64, device=self.device))
+                self._box_key = key
+            box_off, box_L = self._box_default
         nb = int(box_off.shape[0]) - 1
         self._keep = [box_off, box_L]
         for _ in range(3):
@@ -167,6 +173,22 @@ class Solver:
 
     def poll(self) -> int:
         return L.crk_status_poll(self.plan, _stream(), self._wsp)
+
+    # -- CUDA graph of a whole step ---------------------------------------------
+    def capture(self, fn):
+        """Capture ``fn`` (a sequence of this solver's calls with ``check=False``
+        builds) into a CUDA graph and return it; replay with ``graph.replay()``.
+        Every libcrk call is asynchronous and host-synchronisation free, so the
+        whole step -- sort, tree, lists, all sweeps -- becomes one graph."""
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            fn()  # warm-up on a side stream, as torch requires before capture
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
 
     # -- one call for the whole forward path ------------------------------------
     def forward(self, x, h, m, v, u, box_off=None, box_L=None, L_box=1.0, **want):
