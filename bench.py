@@ -154,6 +154,8 @@ def run_ours(args, rank, world):
         if with_adj:
             s.adjoint(src["v"], src["u"], src["ga"], src["gu"], recompute=False, out=grads)
 
+    tuned = s.autotune(dv["m"], dv["v"], dv["u"], dv["ga"] if with_adj else None,
+                       dv["gu"] if with_adj else None, repeats=3) if args.autotune else None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -267,6 +269,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": pairs * world / (e2e_mean * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "autotune": {k: v["variant"] for k, v in tuned.items()} if tuned else None,
         "graph": bool(graph is not None),
         "eager_ms_per_step": round(sum(ms_eager) / len(ms_eager), 4),
         "fwd_pairs_per_s": pairs / (fwd_ms * 1e-3) if fwd_ms > 0 else None,
@@ -409,6 +412,7 @@ def main():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--fwd-only", action="store_true")
     ap.add_argument("--no-graph", dest="graph", action="store_false", default=True)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false", default=True)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-compare", action="store_true", default=True)
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")

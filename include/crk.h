@@ -135,6 +135,22 @@ crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void
                        const void* g_dvdt, const void* g_dudt, void* g_x, void* g_v, void* g_u,
                        void* g_h, int32_t recompute);
 
+/* Autotuner for the launch shapes of the eight neighbor sweeps (volume,
+ * moments, density, rates and the four adjoint sweeps).  Each sweep is
+ * compiled in three variants that differ in the minimum number of resident
+ * blocks per SM (so in the register cap and the occupancy); this call runs
+ * crk_moments, crk_rates and, when g_dvdt and g_dudt are given, crk_adjoint
+ * on the caller's data with each variant `repeats` times, times every sweep
+ * with CUDA events and keeps the fastest variant per sweep in the plan.
+ * Outputs of the trial runs go to the workspace; afterwards the workspace
+ * holds the state of a complete crk_moments + crk_rates call.  choice_out
+ * (optional, host int32[8]) receives the chosen variant per sweep, ms_out
+ * (optional, host float[8][3]) the mean milliseconds of every variant.
+ * Synchronises.  Requires a built workspace. */
+crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
+                        const void* v, const void* u, const void* g_dvdt, const void* g_dudt,
+                        int32_t repeats, int32_t* choice_out, float* ms_out);
+
 /* Test/inspection: the neighbor sets of the last build as CSR in caller order.
  * mode 0: gather set G(i) without the particle itself; mode 1: union set U(i).
  * row_ptr: device int64[n+1]; col: device int32[cap], sorted within a row.

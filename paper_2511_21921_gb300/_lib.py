@@ -65,6 +65,7 @@ _SIGS = {
     "crk_status_string": (C.c_char_p, [C.c_int]),
     "crk_timing_enable": (C.c_int, [_VP, C.c_int32]),
     "crk_timing_read": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_int32)]),
+    "crk_autotune": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int32, _VP, _VP]),
     "crk_volume_static": (C.c_int, [_VP, C.c_int32, C.c_int64, C.c_double, C.c_double, _VP, _VP,
                                     _VP, _VP]),
 }
@@ -190,3 +191,17 @@ def crk_timing_read(plan) -> list[tuple[str, float]]:
 def crk_volume_static(stream, precision, n, L, h_bound, x, h, m, V_out) -> int:
     return load().crk_volume_static(_VP(stream), int(precision), int(n), float(L),
                                     float(h_bound), _VP(x), _VP(h), _VP(m), _VP(V_out))
+
+
+SWEEPS = ("b1_volume", "b2_moments", "c1_density", "c2_rates", "adj_c2", "adj_c1", "adj_b2",
+          "adj_b1")
+
+
+def crk_autotune(plan, stream, ws, m, v, u, g_dvdt, g_dudt, repeats=3):
+    choice = (C.c_int32 * 8)()
+    ms = (C.c_float * 24)()
+    check(load().crk_autotune(_VP(plan), _VP(stream), _VP(ws), _VP(m), _VP(v), _VP(u),
+                              _VP(g_dvdt), _VP(g_dudt), int(repeats), choice, ms),
+          "crk_autotune")
+    return {SWEEPS[q]: {"variant": int(choice[q]), "ms": [round(float(ms[3 * q + k]), 4)
+                                                          for k in range(3)]} for q in range(8)}

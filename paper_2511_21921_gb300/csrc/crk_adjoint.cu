@@ -248,6 +248,7 @@ __global__ void k_adj_prep(const R* __restrict__ gdv, const R* __restrict__ gdu,
 template <class R> struct PassA2 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
+  static constexpr int MB0 = 1, MB1 = 8, MB2 = 10;  // resident-block variants
   static constexpr int QUEUE = Q_A_C2;
   using RC = Rec<R>;
   using AR = ARec<R>;
@@ -504,6 +505,7 @@ template <class R> struct PassA2 {
 template <class R> struct PassA1 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
+  static constexpr int MB0 = 1, MB1 = 8, MB2 = 10;  // resident-block variants
   static constexpr int QUEUE = Q_A_C1;
   using AR = ARec<R>;
   struct Args {
@@ -661,6 +663,7 @@ template <class R> struct PassA1 {
 template <class R> struct PassAB2 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
+  static constexpr int MB0 = 1, MB1 = 10, MB2 = 12;  // resident-block variants
   static constexpr int QUEUE = Q_A_B2;
   using AR = ARec<R>;
   struct Args {
@@ -802,6 +805,7 @@ template <class R> struct PassAB2 {
 template <class R> struct PassAB1 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
+  static constexpr int MB0 = 1, MB1 = 1, MB2 = 1;  // resident-block variants
   static constexpr int QUEUE = Q_A_B1;
   using AR = ARec<R>;
   struct Args {

@@ -78,6 +78,7 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.adj_rec3 = take(R * 12 * N);
   L.adj_acc = take(R * 12 * N);
   L.adj_cbar = take(R * 16 * N);
+  L.tune_out = take(R * 12 * N);  // outputs of the autotuner's trial runs
   L.total = o;
   return L;
 }
@@ -296,6 +297,97 @@ crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void
                             static_cast<float*>(g_x), static_cast<float*>(g_v),
                             static_cast<float*>(g_u), static_cast<float*>(g_h), recompute);
   if (s == CRK_OK && recompute) P.has_rates = true;
+  return s;
+}
+
+crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
+                        const void* v, const void* u, const void* g_dvdt, const void* g_dudt,
+                        int32_t repeats, int32_t* choice_out, float* ms_out) {
+  if (!plan) return CRK_EINVAL;
+  Plan& P = plan->impl;
+  crk_status s = check_ws(P, ws);
+  if (s != CRK_OK) return s;
+  if (P.n > 0 && (!m || !v || !u)) return CRK_EINVAL;
+  if (repeats < 1 || repeats > 100) return CRK_EINVAL;
+  const bool adj = g_dvdt && g_dudt;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  const size_t R = P.p.precision == CRK_FP64 ? 8 : 4;
+  char* out = w + P.ly.tune_out;
+  const size_t N = (size_t)P.n;
+  void* dvdt = out;
+  void* dudt = out + R * 3 * N;
+  void* gx = out + R * 4 * N;
+  void* gv = out + R * 7 * N;
+  void* gu = out + R * 10 * N;
+  void* gh = out + R * 11 * N;
+  static const char* names[8] = {"b1_volume", "b2_moments", "c1_density", "c2_rates",
+                                 "adj_c2",    "adj_c1",     "adj_b2",     "adj_b1"};
+  static const int queues[8] = {Q_B1, Q_B2, Q_C1, Q_C2, Q_A_C2, Q_A_C1, Q_A_B2, Q_A_B1};
+  double tsum[8][3] = {};
+  const bool was_timing = P.timing;
+  auto run = [&]() -> crk_status {
+    crk_status r;
+    if (P.p.precision == CRK_FP64) {
+      r = moments_impl<double>(&P, st, w, static_cast<const double*>(m), nullptr, nullptr);
+      if (r == CRK_OK)
+        r = rates_impl<double>(&P, st, w, static_cast<const double*>(v),
+                               static_cast<const double*>(u), static_cast<double*>(dvdt),
+                               static_cast<double*>(dudt), nullptr, nullptr);
+      if (r == CRK_OK && adj)
+        r = adjoint_impl<double>(&P, st, w, static_cast<const double*>(v),
+                                 static_cast<const double*>(u), static_cast<const double*>(g_dvdt),
+                                 static_cast<const double*>(g_dudt), static_cast<double*>(gx),
+                                 static_cast<double*>(gv), static_cast<double*>(gu),
+                                 static_cast<double*>(gh), 0);
+    } else {
+      r = moments_impl<float>(&P, st, w, static_cast<const float*>(m), nullptr, nullptr);
+      if (r == CRK_OK)
+        r = rates_impl<float>(&P, st, w, static_cast<const float*>(v),
+                              static_cast<const float*>(u), static_cast<float*>(dvdt),
+                              static_cast<float*>(dudt), nullptr, nullptr);
+      if (r == CRK_OK && adj)
+        r = adjoint_impl<float>(&P, st, w, static_cast<const float*>(v),
+                                static_cast<const float*>(u), static_cast<const float*>(g_dvdt),
+                                static_cast<const float*>(g_dudt), static_cast<float*>(gx),
+                                static_cast<float*>(gv), static_cast<float*>(gu),
+                                static_cast<float*>(gh), 0);
+    }
+    return r;
+  };
+  for (int k = 0; k < 3; ++k) {
+    for (int q = 0; q < 8; ++q) P.variant[queues[q]] = k;
+    P.timing = false;
+    if ((s = run()) != CRK_OK) break;
+    for (int r = 0; r < repeats; ++r) {
+      P.timing = true;
+      P.n_timed = 0;
+      if ((s = run()) != CRK_OK) break;
+      crk_kernel_time kt[Plan::kMaxTimed];
+      int32_t cnt = 0;
+      if ((s = crk_timing_read(plan, kt, Plan::kMaxTimed, &cnt)) != CRK_OK) break;
+      for (int i = 0; i < cnt; ++i)
+        for (int q = 0; q < 8; ++q)
+          if (std::strcmp(kt[i].name, names[q]) == 0) tsum[q][k] += kt[i].ms;
+    }
+    if (s != CRK_OK) break;
+  }
+  P.timing = was_timing;
+  P.n_timed = 0;
+  for (int q = 0; q < 8; ++q) {
+    int best = 0;
+    for (int k = 1; k < 3; ++k)
+      if (tsum[q][k] > 0 && tsum[q][k] < tsum[q][best]) best = k;
+    if (s != CRK_OK || (q >= 4 && !adj)) best = 0;
+    P.variant[queues[q]] = best;
+    if (choice_out) choice_out[q] = best;
+    if (ms_out)
+      for (int k = 0; k < 3; ++k) ms_out[q * 3 + k] = (float)(tsum[q][k] / repeats);
+  }
+  if (s == CRK_OK) {
+    P.has_moments = true;
+    P.has_rates = true;
+  }
   return s;
 }
 

@@ -202,7 +202,7 @@ struct Layout {
   size_t gvs = 0, Ds = 0;
   // adjoint
   size_t adj_ab = 0, adj_rec1 = 0, adj_rec2 = 0, adj_rec3 = 0, adj_acc = 0, adj_cbar = 0,
-         mom = 0;
+         mom = 0, tune_out = 0;
   size_t out_x = 0, out_v = 0, out_u = 0, out_h = 0;
 };
 

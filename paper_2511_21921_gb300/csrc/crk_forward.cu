@@ -33,6 +33,7 @@ __global__ void k_pack_b1(const R* __restrict__ xs, const R* __restrict__ m,
 template <class R> struct PassB1 {
   static constexpr bool GATHER = true;
   static constexpr int BLOCK = 256;
+  static constexpr int MB0 = 1, MB1 = 1, MB2 = 1;  // resident-block variants
   static constexpr int QUEUE = Q_B1;
   using RC = Rec<R>;
   struct Args {
@@ -94,6 +95,7 @@ template <class R> struct PassB1 {
 template <class R> struct PassB2 {
   static constexpr bool GATHER = true;
   static constexpr int BLOCK = 256;
+  static constexpr int MB0 = 1, MB1 = 3, MB2 = 4;  // resident-block variants
   static constexpr int QUEUE = Q_B2;
   using RC = Rec<R>;
   struct Args {
@@ -207,6 +209,7 @@ __global__ void k_pack_c1(const R* __restrict__ xs, const R* __restrict__ Vs,
 template <class R> struct PassC1 {
   static constexpr bool GATHER = true;
   static constexpr int BLOCK = 256;
+  static constexpr int MB0 = 1, MB1 = 4, MB2 = 5;  // resident-block variants
   static constexpr int QUEUE = Q_C1;
   using RC = Rec<R>;
   struct Args {
@@ -317,6 +320,7 @@ template <class R> struct PassC1 {
 template <class R> struct PassC2 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 256;
+  static constexpr int MB0 = 1, MB1 = 3, MB2 = 4;  // resident-block variants
   static constexpr int QUEUE = Q_C2;
   using RC = Rec<R>;
   struct Args {

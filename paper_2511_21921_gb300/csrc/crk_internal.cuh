@@ -32,6 +32,7 @@ struct Plan {
   int64_t n = 0;
   int32_t nb = 0;
   Tuning tune[16];
+  int variant[16] = {};  // launch variant per sweep (index into the pass's MB0..MB2)
   // instrumentation
   long long launches = 0;
   bool timing = false;

@@ -39,8 +39,10 @@ inline Common make_common(const Plan* plan, char* ws) {
 }
 
 // Persistent sweep: warps pull 32-particle work items from an atomic queue.
-template <class P>
-__global__ void __launch_bounds__(P::BLOCK) k_sweep(const typename P::Args a) {
+// MINB (minimum resident blocks per SM) sets the register cap; each pass is
+// compiled for three values and the autotuner picks one per plan.
+template <class P, int MINB>
+__global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args a) {
   const int lane = threadIdx.x & 31;
   int32_t* q = &a.c.hdr->queue[P::QUEUE];
   for (;;) {
@@ -293,9 +295,18 @@ template <class R> struct PairC2 {
 template <class P>
 void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const char* name) {
   const int block = P::BLOCK;
-  const int grid = sweep_grid(plan, (const void*)k_sweep<P>, block, P::QUEUE);
+  const int v = plan->variant[P::QUEUE];
   Phase ph(plan, st, name, 1);
-  k_sweep<P><<<grid, block, 0, st>>>(a);
+  if (v == 1) {
+    const int grid = sweep_grid(plan, (const void*)k_sweep<P, P::MB1>, block, P::QUEUE);
+    k_sweep<P, P::MB1><<<grid, block, 0, st>>>(a);
+  } else if (v == 2) {
+    const int grid = sweep_grid(plan, (const void*)k_sweep<P, P::MB2>, block, P::QUEUE);
+    k_sweep<P, P::MB2><<<grid, block, 0, st>>>(a);
+  } else {
+    const int grid = sweep_grid(plan, (const void*)k_sweep<P, P::MB0>, block, P::QUEUE);
+    k_sweep<P, P::MB0><<<grid, block, 0, st>>>(a);
+  }
 }
 
 }  // namespace crk

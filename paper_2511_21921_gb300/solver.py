@@ -76,6 +76,7 @@ class Solver:
         self.params.nbr_cap = int(slots_per_particle)
         L.crk_plan_destroy(self.plan)
         self.plan = L.crk_plan_create(self.params, self.n_max, self.nb_max)
+        self.ws = None  # the layout changed
 
     # -- (a) cell build -----------------------------------------------------
     def cell_build(self, x, h, box_off=None, box_L=None, L_box=1.0, check=True):
@@ -173,6 +174,13 @@ class Solver:
 
     def poll(self) -> int:
         return L.crk_status_poll(self.plan, _stream(), self._wsp)
+
+    # -- autotuner ---------------------------------------------------------------
+    def autotune(self, m, v, u, g_dvdt=None, g_dudt=None, repeats=3) -> dict:
+        """Pick the fastest compiled launch variant of every sweep on this data
+        (after cell_build); the plan keeps the choice.  Synchronises."""
+        return L.crk_autotune(self.plan, _stream(), self._wsp, m.data_ptr(), v.data_ptr(),
+                              u.data_ptr(), _ptr(g_dvdt), _ptr(g_dudt), repeats)
 
     # -- CUDA graph of a whole step ---------------------------------------------
     def capture(self, fn):

@@ -191,3 +191,32 @@ def test_full_size_adjoint_dot_mixed():
     lhs = (ga * tan["dvdt"]).sum() + (gu * tan["dudt"]).sum()
     rhs, scale = _pairing(grads, dirs)
     assert abs(lhs - rhs) <= TOL["mixed"] * scale, (lhs, rhs, scale)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_choices_keep_results(precision):
+    """The autotuner only changes launch shapes (register caps); the compiler may
+    then contract different products into FMAs, so results agree to rounding."""
+    d = _box(seed=23)
+    n = d["h"].shape[0]
+    ga, gu = synth.cotangents(n, seed=11)
+    g0, (dv0, du0), s = _gpu_adjoint(d, precision, ga, gu)
+    t = to_dev(d, precision)
+    dt = t["h"].dtype
+    gat = torch.tensor(ga, dtype=dt, device="cuda")
+    gut = torch.tensor(gu, dtype=dt, device="cuda")
+    tuned = s.autotune(t["m"], t["v"], t["u"], gat, gut, repeats=2)
+    assert set(tuned) == {"b1_volume", "b2_moments", "c1_density", "c2_rates", "adj_c2",
+                          "adj_c1", "adj_b2", "adj_b1"}
+    assert all(v["variant"] in (0, 1, 2) and min(v["ms"]) > 0 for v in tuned.values())
+    dv1, du1, _, _ = s.rates(t["v"], t["u"])
+    g1 = s.adjoint(t["v"], t["u"], gat, gut, recompute=False)
+    torch.cuda.synchronize()
+    tol = 1e-13 if precision == "fp64" else 1e-6
+
+    def rel(a, b):
+        return np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(dv1.double().cpu().numpy(), dv0) < tol
+    assert rel(du1.double().cpu().numpy(), du0) < tol
+    for a, b in zip(g1, g0):
+        assert rel(a.double().cpu().numpy(), b) < tol
