@@ -47,6 +47,35 @@ UNIT_OF = {"b1_volume": "gather", "b2_moments": "gather", "c1_density": "gather"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
+# kernel names of the sweeps as they appear in ncu captures (profiles/*.md)
+PROFILE_KERNEL = {"b1_volume": "PassB1<float>", "b2_moments": "PassB2<float>",
+                  "c1_density": "PassC1<float>", "c2_rates": "PassC2<float>",
+                  "adj_c2": "PassA2<float>", "adj_c1": "PassA1<float>", "adj_b2": "PassAB2<float>",
+                  "adj_b1": "PassAB1<float>"}
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of ``kernel`` from a committed ncu summary, only if
+    that summary was taken on the current sources (same build digest)."""
+    import glob
+    from paper_2511_21921_gb300 import build as B
+    want = PROFILE_KERNEL.get(kernel)
+    if not want:
+        return None
+    digest = B._digest()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        meta = {}
+        with open(path) as fh:
+            for line in fh:
+                if ":" in line and line.split(":", 1)[0] in ("kernel", "build_digest",
+                                                            "dram_bytes_per_launch"):
+                    k, v = line.split(":", 1)
+                    meta[k] = v.strip()
+        if want in meta.get("kernel", "") and meta.get("build_digest") == digest:
+            return int(meta["dram_bytes_per_launch"])
+    return None
+
+
 def _env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -138,8 +167,14 @@ def run_ours(args, rank, world):
     host["ga"] = torch.tensor(gx_h, dtype=dt).pin_memory()
     host["gu"] = torch.tensor(gu_h, dtype=dt).pin_memory()
     dv = {k: t.to(dev) for k, t in host.items()}
-    s = Solver(n, 1, prec, device=dev)
-    s.cell_build(dv["x"], dv["h"], check=True)  # sizes the neighbor lists once
+    nb = 1
+    boxes = (None, None)
+    if "box_off" in d:  # many independent boxes in one call
+        nb = len(d["box_off"]) - 1
+        boxes = (torch.tensor(d["box_off"], dtype=torch.int64, device=dev),
+                 torch.tensor(d["box_L"], dtype=torch.float64, device=dev))
+    s = Solver(n, nb, prec, device=dev)
+    s.cell_build(dv["x"], dv["h"], *boxes, check=True)  # sizes the neighbor lists once
     st0 = s.stats()
     pairs = st0["gather_pairs"]
     upairs = st0["union_pairs"]
@@ -148,7 +183,7 @@ def run_ours(args, rank, world):
     with_adj = not args.fwd_only
 
     def step(src):
-        s.cell_build(src["x"], src["h"], check=False)
+        s.cell_build(src["x"], src["h"], *boxes, check=False)
         s.moments(src["m"])
         s.rates(src["v"], src["u"], out=outs)
         if with_adj:
@@ -250,7 +285,7 @@ def run_ours(args, rank, world):
                          for k in kmean if k in FLOPS_PER_PAIR}
     roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                 "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": profiled_traffic(dom),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                 "flops_per_pair": FLOPS_PER_PAIR[dom], "pairs": units[UNIT_OF[dom]],
                 "kernel_ms": round(kmean[dom], 4)}
@@ -260,7 +295,8 @@ def run_ours(args, rank, world):
         "value": pairs * world / (step_ms * 1e-3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "name": args.workload, "n": n,
+        "config": {"workload": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload,
+                   "name": args.workload, "n": n, "boxes": nb,
                    "gather_pairs": pairs, "union_pairs": upairs,
                    "precision": prec, "step": "build+moments+rates" + ("+adjoint" if with_adj
                                                                        else ""),
@@ -298,11 +334,16 @@ def fp64_compare(args, d, dev):
     ga, gu = synth.cotangents(n, seed=4)
     t64["ga"] = torch.tensor(ga, dtype=torch.float64, device=dev)
     t64["gu"] = torch.tensor(gu, dtype=torch.float64, device=dev)
-    s = Solver(n, 1, "fp64", device=dev)
-    s.cell_build(t64["x"], t64["h"], check=True)
+    nb, boxes = 1, (None, None)
+    if "box_off" in d:
+        nb = len(d["box_off"]) - 1
+        boxes = (torch.tensor(d["box_off"], dtype=torch.int64, device=dev),
+                 torch.tensor(d["box_L"], dtype=torch.float64, device=dev))
+    s = Solver(n, nb, "fp64", device=dev)
+    s.cell_build(t64["x"], t64["h"], *boxes, check=True)
 
     def step():
-        s.cell_build(t64["x"], t64["h"], check=False)
+        s.cell_build(t64["x"], t64["h"], *boxes, check=False)
         s.moments(t64["m"])
         s.rates(t64["v"], t64["u"])
         if not args.fwd_only:

@@ -90,8 +90,9 @@ def test_dot_product_with_relaxation_and_limiter_off():
 
 
 def test_central_differences_of_gpu_forward_fp64():
-    """FD of L = <g, rates> along random directions, step 1e-6, FP64, GPU only."""
-    d = _box(seed=13)
+    """FD of L = <g, rates> along random directions, step 1e-6, FP64, GPU only,
+    on the 32^3 lognormal box."""
+    d = synth.load("lognormal32")
     n = d["h"].shape[0]
     ga, gu = synth.cotangents(n, seed=6)
     grads, _, _ = _gpu_adjoint(d, "fp64", ga, gu)
