@@ -175,7 +175,7 @@ def run_ours(args, rank, world):
         nb = len(d["box_off"]) - 1
         boxes = (torch.tensor(d["box_off"], dtype=torch.int64, device=dev),
                  torch.tensor(d["box_L"], dtype=torch.float64, device=dev))
-    s = Solver(n, nb, prec, device=dev)
+    s = Solver(n, nb, prec, device=dev, prefetch=args.prefetch)
     s.cell_build(dv["x"], dv["h"], *boxes, check=True)  # sizes the neighbor lists once
     st0 = s.stats()
     pairs = st0["gather_pairs"]
@@ -453,6 +453,7 @@ def main():
     ap.add_argument("--fwd-only", action="store_true")
     ap.add_argument("--no-graph", dest="graph", action="store_false", default=True)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false", default=True)
+    ap.add_argument("--prefetch", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-compare", action="store_true", default=True)
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")

@@ -80,7 +80,9 @@ typedef struct {
   int32_t nbr_cap;  /* neighbor-list slots per particle reserved in the workspace; 0 = 192 */
   int32_t block_threads; /* threads per block of the pair sweeps; 0 = autotuned default */
   int32_t blocks_per_sm; /* resident blocks per SM for the persistent sweeps; 0 = default */
-  int32_t reserved[3];
+  int32_t prefetch;      /* sweeps prefetch the neighbor record this many list entries ahead
+                            into L1; 0 = off */
+  int32_t reserved[2];
 } crk_params;
 
 typedef struct crk_plan crk_plan;

@@ -25,7 +25,8 @@ class crk_params(C.Structure):
                 ("eps2", C.c_double), ("eta_crit", C.c_double), ("eta_fold", C.c_double),
                 ("relax_dt", C.c_double), ("limiter", C.c_int32), ("precision", C.c_int32),
                 ("nbr_cap", C.c_int32), ("block_threads", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("blocks_per_sm", C.c_int32), ("prefetch", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class crk_stats(C.Structure):

@@ -291,6 +291,10 @@ template <class R> struct PassA2 {
 #pragma unroll
     for (int k = 0; k < 9; ++k) st.gvb[k] = R(0);
   }
+  __device__ static void prefetch(const Args& a, uint32_t j) {
+    prefetch_record(a.rec_c2, j, RC::C2 * sizeof(R));
+    prefetch_record(a.rec_ab, j, 4 * sizeof(R));
+  }
   __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
     R rj[RC::C2];
     load_rec<RC::C2>(a.rec_c2, j, rj);
@@ -584,6 +588,9 @@ template <class R> struct PassA1 {
     rk_gradient_rev(C, dd, W, g, true, Gb, Cb ? Cb : Cdummy, ddb, Wb, gb);
     hb += wendland_rev(Wb, gb, W, g, gg, r2, ih, dd, ddb);
   }
+  __device__ static void prefetch(const Args& a, uint32_t j) {
+    prefetch_record(a.rec_a1, j, AR::A1 * sizeof(R));
+  }
   __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t e) {
     R rj[AR::A1];
     load_rec<AR::A1>(a.rec_a1, j, rj);
@@ -749,6 +756,9 @@ template <class R> struct PassAB2 {
     for (int k = 0; k < 3; ++k) ddb[k] += db[k];
     return hpart;
   }
+  __device__ static void prefetch(const Args& a, uint32_t j) {
+    prefetch_record(a.rec_a2, j, AR::A2 * sizeof(R));
+  }
   __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t e) {
     R rj[AR::A2];
     load_rec<AR::A2>(a.rec_a2, j, rj);
@@ -830,6 +840,9 @@ template <class R> struct PassAB1 {
     const double L = a.c.box_L[a.c.boxid[s]];
     st.L = (R)L;
     st.halfL = (R)(0.5 * L);
+  }
+  __device__ static void prefetch(const Args& a, uint32_t j) {
+    prefetch_record(a.rec_a3, j, AR::A3 * sizeof(R));
   }
   __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t e) {
     R rj[AR::A3];

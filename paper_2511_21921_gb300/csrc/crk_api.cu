@@ -94,6 +94,7 @@ static bool params_ok(const crk_params& p) {
   if (p.nbr_cap < 0 || p.nbr_cap > 1 << 20) return false;
   if (p.block_threads != 0 && (p.block_threads % 32 != 0 || p.block_threads > 256)) return false;
   if (p.blocks_per_sm < 0 || p.blocks_per_sm > 64) return false;
+  if (p.prefetch < 0 || p.prefetch > 16) return false;
   return true;
 }
 

@@ -60,6 +60,9 @@ template <class R> struct PassB1 {
     st.halfL = (R)(0.5 * L);
     st.sum = R(0);
   }
+  __device__ static void prefetch(const Args& a, uint32_t j) {
+    prefetch_record(a.rec_b1, j, RC::B1 * sizeof(R));
+  }
   __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
     R r[RC::B1];
     load_rec<RC::B1>(a.rec_b1, j, r);
@@ -129,6 +132,9 @@ template <class R> struct PassB2 {
     for (int k = 0; k < 6; ++k) { st.m2[k] = R(0); st.S2[k] = R(0); }
 #pragma unroll
     for (int k = 0; k < 10; ++k) st.S3[k] = R(0);
+  }
+  __device__ static void prefetch(const Args& a, uint32_t j) {
+    prefetch_record(a.rec_b2, j, RC::B2 * sizeof(R));
   }
   __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
     R r[RC::B2];
@@ -251,6 +257,9 @@ template <class R> struct PassC1 {
 #pragma unroll
     for (int k = 0; k < 9; ++k) st.gv[k] = R(0);
   }
+  __device__ static void prefetch(const Args& a, uint32_t j) {
+    prefetch_record(a.rec_c1, j, RC::C1 * sizeof(R));
+  }
   __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
     R r[RC::C1];
     load_rec<RC::C1>(a.rec_c1, j, r);
@@ -344,6 +353,9 @@ template <class R> struct PassC2 {
     st.halfL = (R)(0.5 * L);
     st.a[0] = st.a[1] = st.a[2] = R(0);
     st.e = Acc<R>();
+  }
+  __device__ static void prefetch(const Args& a, uint32_t j) {
+    prefetch_record(a.rec_c2, j, RC::C2 * sizeof(R));
   }
   __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
     R rj[RC::C2];

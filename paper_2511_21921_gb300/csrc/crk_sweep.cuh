@@ -18,7 +18,16 @@ struct Common {
   const double* __restrict__ box_L;
   const int32_t* __restrict__ perm;
   int64_t cap_pp;  // list slots per particle: gather part from the front, scatter-only from the back
+  int pf;          // prefetch distance in list entries (0 = off)
 };
+
+// Ask L1 for the cache lines of neighbor j's record (base + j*bytes, `bytes`
+// long) ahead of its use; no register is tied up.
+__device__ __forceinline__ void prefetch_record(const void* base, uint32_t j, int bytes) {
+  const char* p = static_cast<const char*>(base) + (size_t)j * bytes;
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+  if (bytes > 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(p + bytes - 4));
+}
 
 inline Common make_common(const Plan* plan, char* ws) {
   const Layout& Ly = plan->ly;
@@ -35,6 +44,7 @@ inline Common make_common(const Plan* plan, char* ws) {
   c.box_L = reinterpret_cast<const double*>(ws + Ly.box_L);
   c.perm = reinterpret_cast<const int32_t*>(ws + Ly.perm);
   c.cap_pp = Ly.cap_pp;
+  c.pf = plan->p.prefetch;
   return c;
 }
 
@@ -63,7 +73,9 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
     if (P::GATHER) {
       // gather part only: the same row of every lane is one 128-byte line
       const int wg = a.c.wlen_g[w];
+      const int pf = a.c.pf;
       for (int k = 0; k < wg; ++k) {
+        if (pf && k + pf < lg) P::prefetch(a, __ldg(col + (int64_t)(k + pf) * 32) & kIdxMask);
         const uint32_t e = __ldg(col + (int64_t)k * 32);
         if (k < lg) P::pair(a, st, e & kIdxMask, e);
       }
@@ -73,7 +85,13 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
       // parts
       const int tot = lg + ls;
       const int wmax = __reduce_max_sync(kFull, tot);
+      const int pf = a.c.pf;
       for (int k = 0; k < wmax; ++k) {
+        if (pf && k + pf < tot) {
+          const int kp = k + pf;
+          const int64_t sp = kp < lg ? kp : a.c.cap_pp - 1 - (kp - lg);
+          P::prefetch(a, __ldg(col + sp * 32) & kIdxMask);
+        }
         if (k < tot) {
           const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
           const uint32_t e = __ldg(col + slot * 32);
