@@ -9,3 +9,4 @@ from .oracle import (  # noqa: F401
     OracleParams, build, default_params, forward, jvp, neighbors, kernel, num_threads,
     PARITY_UNPINNED,
 )
+from . import integrate  # noqa: F401,E402
