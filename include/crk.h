@@ -18,6 +18,10 @@
  *                      positions, velocities, internal energies and smoothing
  *                      lengths (no counterpart in the paper; it gives the
  *                      subgrid calibration of Sec. 3 a gradient).
+ *   crk_hdot, crk_kick, crk_kick_refined, crk_drift
+ *                   -- the time step around the rates: smoothing-length rate
+ *                      and exponential drifts (App. B.1), kick-drift-kick with
+ *                      refined kicks and parabolic passive drifts (App. B.2).
  *
  * Conventions shared by every entry point:
  *  - Device pointers are owned by the caller; the library never allocates
@@ -136,6 +140,68 @@ crk_status crk_rates(crk_plan* plan, crk_stream_t stream, void* ws, const void* 
 crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void* v, const void* u,
                        const void* g_dvdt, const void* g_dudt, void* g_x, void* g_v, void* g_u,
                        void* g_h, int32_t recompute);
+
+/* ---- Time step around the rates (App. B.1 and B.2) -------------------------
+ * A kick-drift-kick step is: crk_kick (half kick with the rates of the last
+ * evaluation), crk_drift (positions, smoothing lengths), crk_cell_build,
+ * crk_moments, crk_rates at the new positions, crk_hdot, crk_kick (second
+ * half kick).  These four calls are one pass over the particles each; they
+ * neither read nor write the workspace except crk_hdot, which reads it.
+ * Element types follow params.precision as everywhere else. */
+
+/* (e) Smoothing-length rate (App. B.1, Smoothing Length Integration):
+ *   hdot_i = (h^T_i - h_i) / dt_a + h_i (div v)_i / 3,
+ *   h^T_i  = h_i (1 - lambda + lambda Delta_N),  Delta_N = n_h V_i^(1/3) / h_i,
+ * with V_i the volume of the last crk_moments, (div v)_i the trace of the
+ * velocity gradient of the last crk_rates and h_i the smoothing length of the
+ * last crk_cell_build.  dt_a > 0: the active time step; lambda: the Thacker
+ * weight; n_h > 0: target particles per kernel radius (4 for the paper's
+ * gas).  Optional outputs, device real[n] in caller order: hdot_out;
+ * hrate_out = hdot_i / h_i (the logarithmic rate that crk_drift takes);
+ * div_out = (div v)_i.  CRK_ESTATE before a crk_rates on this workspace. */
+crk_status crk_hdot(crk_plan* plan, crk_stream_t stream, void* ws, double dt_a, double lambda,
+                    double n_h, void* hdot_out, void* hrate_out, void* div_out);
+
+/* (f) Kick (App. B.2, K): v_out = v0 + dt a and, when u_out is given,
+ * u_out = u0 + dt dudt.  dt is the kick length (dt_a/2 for a half kick; the
+ * refined first half kick of App. B.2 is this call from v0 with dt_b/2).
+ * active: optional device uint8[n]; particles with active[i] == 0 keep v0 (and
+ * u0).  v0, a, v_out: device real[3][n]; u0, dudt, u_out: device real[n].
+ * Outputs may alias inputs (in-place kicks).  n <= the plan's n_max. */
+crk_status crk_kick(crk_plan* plan, crk_stream_t stream, int64_t n, double dt,
+                    const uint8_t* active, const void* v0, const void* a, void* v_out,
+                    const void* u0, const void* dudt, void* u_out);
+
+/* (g) Completion of a refined step (App. B.2, Adaptive Kick Corrections):
+ *   v_out = v0 + a0 (dt_b - dt_c) + (a0 + a1) dt_c / 2
+ * (and likewise u from u0, du0, du1 when u_out is given): constant a0 until
+ * the last dt_c of the refined interval dt_b, then a plain kick-drift-kick
+ * average.  0 <= dt_c <= dt_b.  Layouts and `active` as for crk_kick. */
+crk_status crk_kick_refined(crk_plan* plan, crk_stream_t stream, int64_t n, double dt_b,
+                            double dt_c, const uint8_t* active, const void* v0, const void* a0,
+                            const void* a1, void* v_out, const void* u0, const void* du0,
+                            const void* du1, void* u_out);
+
+/* (h) Drift by dt >= 0 (App. B.2, D), in place, and the drifts of App. B.1.
+ *   x: device double[3][n], updated in double as x + v dt and wrapped into the
+ *      particle's box [0, L) (box_off/box_L as for crk_cell_build); a particle
+ *      that moves more than one box side is left outside and the next
+ *      crk_cell_build reports CRK_EDOMAIN.
+ *   v is v_half (device real[3][n]) or, when a0 (device real[3][n]) is given,
+ *      the local half-step velocity of a passive sub-step
+ *      v_half + a0 [t_elapse_i + (dt - dt_a_i)/2]; dt_a and t_elapse are
+ *      optional device double[n] (the particle's active interval and the time
+ *      of it already drifted; defaults dt and 0, an active particle).
+ *   h, hrate: optional pair, device real[n]: h <- h exp(hrate dt) with hrate
+ *      the logarithmic rate from crk_hdot.
+ *   V: optional device real[n] (needs h and n_h > 0): V <- (h / n_h)^3.
+ *   rho, div: optional pair, device real[n]: rho <- rho exp(-div dt).
+ * In the mixed form the displacement v dt is a float, added in double. */
+crk_status crk_drift(crk_plan* plan, crk_stream_t stream, int64_t n, int32_t n_boxes,
+                     const int64_t* box_off, const double* box_L, double dt, double* x,
+                     const void* v_half, const void* a0, const double* dt_a,
+                     const double* t_elapse, void* h, const void* hrate, double n_h, void* V,
+                     void* rho, const void* div);
 
 /* Autotuner for the launch shapes of the eight neighbor sweeps (volume,
  * moments, density, rates and the four adjoint sweeps).  Each sweep is

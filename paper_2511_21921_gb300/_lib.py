@@ -69,6 +69,12 @@ _SIGS = {
     "crk_autotune": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int32, _VP, _VP]),
     "crk_volume_static": (C.c_int, [_VP, C.c_int32, C.c_int64, C.c_double, C.c_double, _VP, _VP,
                                     _VP, _VP]),
+    "crk_hdot": (C.c_int, [_VP, _VP, _VP, C.c_double, C.c_double, C.c_double, _VP, _VP, _VP]),
+    "crk_kick": (C.c_int, [_VP, _VP, C.c_int64, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "crk_kick_refined": (C.c_int, [_VP, _VP, C.c_int64, C.c_double, C.c_double, _VP, _VP, _VP,
+                                   _VP, _VP, _VP, _VP, _VP, _VP]),
+    "crk_drift": (C.c_int, [_VP, _VP, C.c_int64, C.c_int32, _VP, _VP, C.c_double, _VP, _VP, _VP,
+                            _VP, _VP, _VP, _VP, C.c_double, _VP, _VP, _VP]),
 }
 CRK_STATIC_MAX_PARTICLES = 65536
 
@@ -192,6 +198,32 @@ def crk_timing_read(plan) -> list[tuple[str, float]]:
 def crk_volume_static(stream, precision, n, L, h_bound, x, h, m, V_out) -> int:
     return load().crk_volume_static(_VP(stream), int(precision), int(n), float(L),
                                     float(h_bound), _VP(x), _VP(h), _VP(m), _VP(V_out))
+
+
+def crk_hdot(plan, stream, ws, dt_a, lam, n_h, hdot_out=None, hrate_out=None,
+             div_out=None) -> int:
+    return load().crk_hdot(_VP(plan), _VP(stream), _VP(ws), float(dt_a), float(lam),
+                           float(n_h), _VP(hdot_out), _VP(hrate_out), _VP(div_out))
+
+
+def crk_kick(plan, stream, n, dt, active, v0, a, v_out, u0=None, dudt=None, u_out=None) -> int:
+    return load().crk_kick(_VP(plan), _VP(stream), int(n), float(dt), _VP(active), _VP(v0),
+                           _VP(a), _VP(v_out), _VP(u0), _VP(dudt), _VP(u_out))
+
+
+def crk_kick_refined(plan, stream, n, dt_b, dt_c, active, v0, a0, a1, v_out, u0=None, du0=None,
+                     du1=None, u_out=None) -> int:
+    return load().crk_kick_refined(_VP(plan), _VP(stream), int(n), float(dt_b), float(dt_c),
+                                   _VP(active), _VP(v0), _VP(a0), _VP(a1), _VP(v_out), _VP(u0),
+                                   _VP(du0), _VP(du1), _VP(u_out))
+
+
+def crk_drift(plan, stream, n, n_boxes, box_off, box_L, dt, x, v_half, a0=None, dt_a=None,
+              t_elapse=None, h=None, hrate=None, n_h=0.0, V=None, rho=None, div=None) -> int:
+    return load().crk_drift(_VP(plan), _VP(stream), int(n), int(n_boxes), _VP(box_off),
+                            _VP(box_L), float(dt), _VP(x), _VP(v_half), _VP(a0), _VP(dt_a),
+                            _VP(t_elapse), _VP(h), _VP(hrate), float(n_h), _VP(V), _VP(rho),
+                            _VP(div))
 
 
 SWEEPS = ("b1_volume", "b2_moments", "c1_density", "c2_rates", "adj_c2", "adj_c1", "adj_b2",

@@ -72,6 +72,18 @@ class Solver:
         base = self.ws.data_ptr()
         return base + ((-base) % 256)
 
+    def _boxes(self, n, box_off, box_L, L_box):
+        if box_off is not None:
+            return box_off, box_L
+        # single box: made once and reused (no host copy inside graph capture)
+        key = (n, float(L_box))
+        if getattr(self, "_box_key", None) != key:
+            self._box_default = (
+                torch.tensor([0, n], dtype=torch.int64, device=self.device),
+                torch.tensor([float(L_box)], dtype=torch.float64, device=self.device))
+            self._box_key = key
+        return self._box_default
+
     def _regrow(self, slots_per_particle):
         self.params.nbr_cap = int(slots_per_particle)
         L.crk_plan_destroy(self.plan)
@@ -86,15 +98,7 @@ class Solver:
         n = int(h.shape[0])
         assert x.dtype == torch.float64 and x.shape == (3, n) and x.is_contiguous()
         assert h.dtype == self.dtype and h.is_contiguous()
-        if box_off is None:
-            # single box: made once and reused (no host copy inside graph capture)
-            key = (n, float(L_box))
-            if getattr(self, "_box_key", None) != key:
-                self._box_default = (
-                    torch.tensor([0, n], dtype=torch.int64, device=self.device),
-                    torch.tensor([float(L_box)], dtype=torch.float64, device=self.device))
-                self._box_key = key
-            box_off, box_L = self._box_default
+        box_off, box_L = self._boxes(n, box_off, box_L, L_box)
         nb = int(box_off.shape[0]) - 1
         self._keep = [box_off, box_L]
         for _ in range(3):
@@ -153,6 +157,80 @@ class Solver:
                               gu.data_ptr(), gh.data_ptr(), 1 if recompute else 0),
                 "crk_adjoint")
         return gx, gv, gu, gh
+
+    # -- (e)-(h) time step around the rates --------------------------------------
+    def hdot(self, dt_a, lam, n_h, out=None):
+        """(hdot, hdot/h, div v) of the last rates evaluation, caller order."""
+        n = self.n
+        if out is None:
+            out = tuple(torch.empty(n, dtype=self.dtype, device=self.device) for _ in range(3))
+        hd, hr, dv = out
+        L.check(L.crk_hdot(self.plan, _stream(), self._wsp, dt_a, lam, n_h, _ptr(hd), _ptr(hr),
+                           _ptr(dv)), "crk_hdot")
+        return hd, hr, dv
+
+    def kick(self, dt, v0, a, u0=None, dudt=None, v_out=None, u_out=None, active=None):
+        """v0 + dt a (and u0 + dt dudt); in place when no outputs are given."""
+        n = int(v0.shape[1])
+        v_out = v0 if v_out is None else v_out
+        if u0 is not None and u_out is None:
+            u_out = u0
+        L.check(L.crk_kick(self.plan, _stream(), n, dt, _ptr(active), v0.data_ptr(), a.data_ptr(),
+                           v_out.data_ptr(), _ptr(u0), _ptr(dudt), _ptr(u_out)), "crk_kick")
+        return v_out, u_out
+
+    def kick_refined(self, dt_b, dt_c, v0, a0, a1, u0=None, du0=None, du1=None, v_out=None,
+                     u_out=None, active=None):
+        n = int(v0.shape[1])
+        v_out = v0 if v_out is None else v_out
+        if u0 is not None and u_out is None:
+            u_out = u0
+        L.check(L.crk_kick_refined(self.plan, _stream(), n, dt_b, dt_c, _ptr(active),
+                                   v0.data_ptr(), a0.data_ptr(), a1.data_ptr(), v_out.data_ptr(),
+                                   _ptr(u0), _ptr(du0), _ptr(du1), _ptr(u_out)),
+                "crk_kick_refined")
+        return v_out, u_out
+
+    def drift(self, dt, x, v_half, a0=None, dt_a=None, t_elapse=None, h=None, hrate=None,
+              n_h=0.0, V=None, rho=None, div=None, box_off=None, box_L=None, L_box=1.0):
+        """In-place drift of x (and h, V, rho when given)."""
+        n = int(x.shape[1])
+        box_off, box_L = self._boxes(n, box_off, box_L, L_box)
+        L.check(L.crk_drift(self.plan, _stream(), n, int(box_off.shape[0]) - 1, box_off.data_ptr(),
+                            box_L.data_ptr(), dt, x.data_ptr(), v_half.data_ptr(), _ptr(a0),
+                            _ptr(dt_a), _ptr(t_elapse), _ptr(h), _ptr(hrate), n_h, _ptr(V),
+                            _ptr(rho), _ptr(div)), "crk_drift")
+        return x
+
+    def kdk_init(self, x, v, u, h, m, dt_a, lam, n_h, box_off=None, box_L=None, L_box=1.0):
+        """Rates and smoothing-length rate at the start of the first step."""
+        self.cell_build(x, h, box_off, box_L, L_box)
+        self.moments(m)
+        a, du, _, _ = self.rates(v, u)
+        _, hr, dv = self.hdot(dt_a, lam, n_h)
+        return {"a": a, "du": du, "hrate": hr, "div": dv}
+
+    def kdk_step(self, x, v, u, h, m, d, dt, lam, n_h, box_off=None, box_L=None, L_box=1.0,
+                 check=True, scratch=None):
+        """One global kick-drift-kick step of length dt, in place on x, v, u, h
+        and on the derivative set d (rates and hrate of the previous
+        evaluation in, of the new one out).  Half kick; drift of x and h; rates
+        at the new positions with the predicted velocity and energy
+        v_half + a dt/2, u_half + du dt/2; smoothing-length rate; half kick.
+        With fixed tensors and check=False the step can be graph-captured."""
+        half = 0.5 * dt
+        if scratch is None:
+            scratch = (torch.empty_like(v), torch.empty_like(u))
+        v_p, u_p = scratch
+        self.kick(half, v, d["a"], u, d["du"])
+        self.drift(dt, x, v, h=h, hrate=d["hrate"], box_off=box_off, box_L=box_L, L_box=L_box)
+        self.kick(half, v, d["a"], u, d["du"], v_out=v_p, u_out=u_p)
+        self.cell_build(x, h, box_off, box_L, L_box, check=check)
+        self.moments(m)
+        self.rates(v_p, u_p, out=(d["a"], d["du"]))
+        self.hdot(dt, lam, n_h, out=(None, d["hrate"], d["div"]))
+        self.kick(half, v, d["a"], u, d["du"])
+        return d
 
     # -- inspection -------------------------------------------------------------
     def neighbors_csr(self, mode="gather"):
