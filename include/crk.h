@@ -205,16 +205,19 @@ crk_status crk_drift(crk_plan* plan, crk_stream_t stream, int64_t n, int32_t n_b
 
 /* Autotuner for the launch shapes of the eight neighbor sweeps (volume,
  * moments, density, rates and the four adjoint sweeps).  Each sweep is
- * compiled in three variants that differ in the minimum number of resident
- * blocks per SM (so in the register cap and the occupancy); this call runs
- * crk_moments, crk_rates and, when g_dvdt and g_dudt are given, crk_adjoint
- * on the caller's data with each variant `repeats` times, times every sweep
- * with CUDA events and keeps the fastest variant per sweep in the plan.
- * Outputs of the trial runs go to the workspace; afterwards the workspace
- * holds the state of a complete crk_moments + crk_rates call.  choice_out
- * (optional, host int32[8]) receives the chosen variant per sweep, ms_out
- * (optional, host float[8][3]) the mean milliseconds of every variant.
- * Synchronises.  Requires a built workspace. */
+ * compiled in CRK_TUNE_VARIANTS variants: three minimum numbers of resident
+ * blocks per SM (so three register caps and occupancies), each with the
+ * neighbor records read straight from global memory (variants 0-2) or copied
+ * ahead through a per-thread shared-memory ring with cp.async (variants 3-5).
+ * This call runs crk_moments, crk_rates and, when g_dvdt and g_dudt are given,
+ * crk_adjoint on the caller's data with each variant `repeats` times, times
+ * every sweep with CUDA events and keeps the fastest variant per sweep in the
+ * plan.  Outputs of the trial runs go to the workspace; afterwards the
+ * workspace holds the state of a complete crk_moments + crk_rates call.
+ * choice_out (optional, host int32[8]) receives the chosen variant per sweep,
+ * ms_out (optional, host float[8][CRK_TUNE_VARIANTS]) the mean milliseconds of
+ * every variant.  Synchronises.  Requires a built workspace. */
+#define CRK_TUNE_VARIANTS 6
 crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
                         const void* v, const void* u, const void* g_dvdt, const void* g_dudt,
                         int32_t repeats, int32_t* choice_out, float* ms_out);

@@ -77,6 +77,7 @@ _SIGS = {
                             _VP, _VP, _VP, _VP, C.c_double, _VP, _VP, _VP]),
 }
 CRK_STATIC_MAX_PARTICLES = 65536
+CRK_TUNE_VARIANTS = 6  # launch variants per sweep (include/crk.h)
 
 _lib = None
 
@@ -231,10 +232,11 @@ SWEEPS = ("b1_volume", "b2_moments", "c1_density", "c2_rates", "adj_c2", "adj_c1
 
 
 def crk_autotune(plan, stream, ws, m, v, u, g_dvdt, g_dudt, repeats=3):
+    nv = CRK_TUNE_VARIANTS
     choice = (C.c_int32 * 8)()
-    ms = (C.c_float * 24)()
+    ms = (C.c_float * (8 * nv))()
     check(load().crk_autotune(_VP(plan), _VP(stream), _VP(ws), _VP(m), _VP(v), _VP(u),
                               _VP(g_dvdt), _VP(g_dudt), int(repeats), choice, ms),
           "crk_autotune")
-    return {SWEEPS[q]: {"variant": int(choice[q]), "ms": [round(float(ms[3 * q + k]), 4)
-                                                          for k in range(3)]} for q in range(8)}
+    return {SWEEPS[q]: {"variant": int(choice[q]), "ms": [round(float(ms[nv * q + k]), 4)
+                                                          for k in range(nv)]} for q in range(8)}

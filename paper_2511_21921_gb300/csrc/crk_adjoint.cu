@@ -250,6 +250,8 @@ template <class R> struct PassA2 {
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 8, MB2 = 10;  // resident-block variants
   static constexpr int QUEUE = Q_A_C2;
+  using Real = R;
+  static constexpr int SW0 = Rec<R>::C2, SW1 = 4;  // words staged per neighbor
   using RC = Rec<R>;
   using AR = ARec<R>;
   struct Args {
@@ -291,15 +293,10 @@ template <class R> struct PassA2 {
 #pragma unroll
     for (int k = 0; k < 9; ++k) st.gvb[k] = R(0);
   }
-  __device__ static void prefetch(const Args& a, uint32_t j) {
-    prefetch_record(a.rec_c2, j, RC::C2 * sizeof(R));
-    prefetch_record(a.rec_ab, j, 4 * sizeof(R));
-  }
-  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
-    R rj[RC::C2];
-    load_rec<RC::C2>(a.rec_c2, j, rj);
-    R abj[4];
-    load_rec<4>(a.rec_ab, j, abj);
+  __device__ static const R* src0(const Args& a) { return a.rec_c2; }
+  __device__ static const R* src1(const Args& a) { return a.rec_ab; }
+  __device__ static void pair_s(const Args& a, State& st, const R* rj, const R* abj, uint32_t j,
+                                uint32_t) {
     const R* ri = st.ri;
     R d[3];
     separation(ri, rj, st.L, st.halfL, d);
@@ -511,6 +508,8 @@ template <class R> struct PassA1 {
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 8, MB2 = 10;  // resident-block variants
   static constexpr int QUEUE = Q_A_C1;
+  using Real = R;
+  static constexpr int SW0 = ARec<R>::A1, SW1 = 0;  // words staged per neighbor
   using AR = ARec<R>;
   struct Args {
     Common c;
@@ -588,12 +587,10 @@ template <class R> struct PassA1 {
     rk_gradient_rev(C, dd, W, g, true, Gb, Cb ? Cb : Cdummy, ddb, Wb, gb);
     hb += wendland_rev(Wb, gb, W, g, gg, r2, ih, dd, ddb);
   }
-  __device__ static void prefetch(const Args& a, uint32_t j) {
-    prefetch_record(a.rec_a1, j, AR::A1 * sizeof(R));
-  }
-  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t e) {
-    R rj[AR::A1];
-    load_rec<AR::A1>(a.rec_a1, j, rj);
+  __device__ static const R* src0(const Args& a) { return a.rec_a1; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static void pair_s(const Args& a, State& st, const R* rj, const R*, uint32_t j,
+                                uint32_t e) {
     R d[3];
     separation(st.ra, rj, st.L, st.halfL, d);
     const R r2 = dot3(d, d);
@@ -672,6 +669,8 @@ template <class R> struct PassAB2 {
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 10, MB2 = 12;  // resident-block variants
   static constexpr int QUEUE = Q_A_B2;
+  using Real = R;
+  static constexpr int SW0 = ARec<R>::A2, SW1 = 0;  // words staged per neighbor
   using AR = ARec<R>;
   struct Args {
     Common c;
@@ -756,12 +755,10 @@ template <class R> struct PassAB2 {
     for (int k = 0; k < 3; ++k) ddb[k] += db[k];
     return hpart;
   }
-  __device__ static void prefetch(const Args& a, uint32_t j) {
-    prefetch_record(a.rec_a2, j, AR::A2 * sizeof(R));
-  }
-  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t e) {
-    R rj[AR::A2];
-    load_rec<AR::A2>(a.rec_a2, j, rj);
+  __device__ static const R* src0(const Args& a) { return a.rec_a2; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static void pair_s(const Args& a, State& st, const R* rj, const R*, uint32_t j,
+                                uint32_t e) {
     R d[3];
     separation(st.ra, rj, st.L, st.halfL, d);
     const R r2 = dot3(d, d);
@@ -817,6 +814,8 @@ template <class R> struct PassAB1 {
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 1, MB2 = 1;  // resident-block variants
   static constexpr int QUEUE = Q_A_B1;
+  using Real = R;
+  static constexpr int SW0 = ARec<R>::A3, SW1 = 0;  // words staged per neighbor
   using AR = ARec<R>;
   struct Args {
     Common c;
@@ -841,12 +840,10 @@ template <class R> struct PassAB1 {
     st.L = (R)L;
     st.halfL = (R)(0.5 * L);
   }
-  __device__ static void prefetch(const Args& a, uint32_t j) {
-    prefetch_record(a.rec_a3, j, AR::A3 * sizeof(R));
-  }
-  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t e) {
-    R rj[AR::A3];
-    load_rec<AR::A3>(a.rec_a3, j, rj);
+  __device__ static const R* src0(const Args& a) { return a.rec_a3; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static void pair_s(const Args& a, State& st, const R* rj, const R*, uint32_t j,
+                                uint32_t e) {
     R d[3];
     separation(st.ra, rj, st.L, st.halfL, d);
     const R r2 = dot3(d, d);

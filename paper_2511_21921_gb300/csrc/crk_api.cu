@@ -325,7 +325,7 @@ crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const voi
   static const char* names[8] = {"b1_volume", "b2_moments", "c1_density", "c2_rates",
                                  "adj_c2",    "adj_c1",     "adj_b2",     "adj_b1"};
   static const int queues[8] = {Q_B1, Q_B2, Q_C1, Q_C2, Q_A_C2, Q_A_C1, Q_A_B2, Q_A_B1};
-  double tsum[8][3] = {};
+  double tsum[8][CRK_TUNE_VARIANTS] = {};
   const bool was_timing = P.timing;
   auto run = [&]() -> crk_status {
     crk_status r;
@@ -356,7 +356,7 @@ crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const voi
     }
     return r;
   };
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < CRK_TUNE_VARIANTS; ++k) {
     for (int q = 0; q < 8; ++q) P.variant[queues[q]] = k;
     P.timing = false;
     if ((s = run()) != CRK_OK) break;
@@ -377,13 +377,14 @@ crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const voi
   P.n_timed = 0;
   for (int q = 0; q < 8; ++q) {
     int best = 0;
-    for (int k = 1; k < 3; ++k)
+    for (int k = 1; k < CRK_TUNE_VARIANTS; ++k)
       if (tsum[q][k] > 0 && tsum[q][k] < tsum[q][best]) best = k;
     if (s != CRK_OK || (q >= 4 && !adj)) best = 0;
     P.variant[queues[q]] = best;
     if (choice_out) choice_out[q] = best;
     if (ms_out)
-      for (int k = 0; k < 3; ++k) ms_out[q * 3 + k] = (float)(tsum[q][k] / repeats);
+      for (int k = 0; k < CRK_TUNE_VARIANTS; ++k)
+        ms_out[q * CRK_TUNE_VARIANTS + k] = (float)(tsum[q][k] / repeats);
   }
   if (s == CRK_OK) {
     P.has_moments = true;

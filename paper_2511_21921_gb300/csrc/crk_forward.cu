@@ -35,6 +35,8 @@ template <class R> struct PassB1 {
   static constexpr int BLOCK = 256;
   static constexpr int MB0 = 1, MB1 = 1, MB2 = 1;  // resident-block variants
   static constexpr int QUEUE = Q_B1;
+  using Real = R;
+  static constexpr int SW0 = Rec<R>::B1, SW1 = 0;  // words staged per neighbor
   using RC = Rec<R>;
   struct Args {
     Common c;
@@ -60,12 +62,10 @@ template <class R> struct PassB1 {
     st.halfL = (R)(0.5 * L);
     st.sum = R(0);
   }
-  __device__ static void prefetch(const Args& a, uint32_t j) {
-    prefetch_record(a.rec_b1, j, RC::B1 * sizeof(R));
-  }
-  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
-    R r[RC::B1];
-    load_rec<RC::B1>(a.rec_b1, j, r);
+  __device__ static const R* src0(const Args& a) { return a.rec_b1; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static void pair_s(const Args& a, State& st, const R* r, const R*, uint32_t j,
+                                uint32_t) {
     R d[3];
     separation(st.x, r, st.L, st.halfL, d);
     R W, g;
@@ -100,6 +100,8 @@ template <class R> struct PassB2 {
   static constexpr int BLOCK = 256;
   static constexpr int MB0 = 1, MB1 = 3, MB2 = 4;  // resident-block variants
   static constexpr int QUEUE = Q_B2;
+  using Real = R;
+  static constexpr int SW0 = Rec<R>::B2, SW1 = 0;  // words staged per neighbor
   using RC = Rec<R>;
   struct Args {
     Common c;
@@ -133,12 +135,10 @@ template <class R> struct PassB2 {
 #pragma unroll
     for (int k = 0; k < 10; ++k) st.S3[k] = R(0);
   }
-  __device__ static void prefetch(const Args& a, uint32_t j) {
-    prefetch_record(a.rec_b2, j, RC::B2 * sizeof(R));
-  }
-  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
-    R r[RC::B2];
-    load_rec<RC::B2>(a.rec_b2, j, r);
+  __device__ static const R* src0(const Args& a) { return a.rec_b2; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static void pair_s(const Args& a, State& st, const R* r, const R*, uint32_t j,
+                                uint32_t) {
     R d[3];
     separation(st.x, r, st.L, st.halfL, d);
     R W, g;
@@ -217,6 +217,8 @@ template <class R> struct PassC1 {
   static constexpr int BLOCK = 256;
   static constexpr int MB0 = 1, MB1 = 4, MB2 = 5;  // resident-block variants
   static constexpr int QUEUE = Q_C1;
+  using Real = R;
+  static constexpr int SW0 = Rec<R>::C1, SW1 = 0;  // words staged per neighbor
   using RC = Rec<R>;
   struct Args {
     Common c;
@@ -257,12 +259,10 @@ template <class R> struct PassC1 {
 #pragma unroll
     for (int k = 0; k < 9; ++k) st.gv[k] = R(0);
   }
-  __device__ static void prefetch(const Args& a, uint32_t j) {
-    prefetch_record(a.rec_c1, j, RC::C1 * sizeof(R));
-  }
-  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
-    R r[RC::C1];
-    load_rec<RC::C1>(a.rec_c1, j, r);
+  __device__ static const R* src0(const Args& a) { return a.rec_c1; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static void pair_s(const Args& a, State& st, const R* r, const R*, uint32_t j,
+                                uint32_t) {
     R d[3];
     separation(st.x, r, st.L, st.halfL, d);
     R W, g;
@@ -328,9 +328,11 @@ template <class R> struct PassC1 {
 // ===========================================================================
 template <class R> struct PassC2 {
   static constexpr bool GATHER = false;
-  static constexpr int BLOCK = 256;
-  static constexpr int MB0 = 1, MB1 = 3, MB2 = 4;  // resident-block variants
+  static constexpr int BLOCK = 128;
+  static constexpr int MB0 = 2, MB1 = 4, MB2 = 5;  // resident-block variants
   static constexpr int QUEUE = Q_C2;
+  using Real = R;
+  static constexpr int SW0 = Rec<R>::C2, SW1 = 0;  // words staged per neighbor
   using RC = Rec<R>;
   struct Args {
     Common c;
@@ -354,12 +356,10 @@ template <class R> struct PassC2 {
     st.a[0] = st.a[1] = st.a[2] = R(0);
     st.e = Acc<R>();
   }
-  __device__ static void prefetch(const Args& a, uint32_t j) {
-    prefetch_record(a.rec_c2, j, RC::C2 * sizeof(R));
-  }
-  __device__ static void pair(const Args& a, State& st, uint32_t j, uint32_t) {
-    R rj[RC::C2];
-    load_rec<RC::C2>(a.rec_c2, j, rj);
+  __device__ static const R* src0(const Args& a) { return a.rec_c2; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static void pair_s(const Args& a, State& st, const R* rj, const R*, uint32_t,
+                                uint32_t) {
     R d[3];
     separation(st.ri, rj, st.L, st.halfL, d);
     const R r2 = dot3(d, d);
@@ -383,14 +383,12 @@ template <class R> struct PassC2 {
 // ===========================================================================
 // launch helpers and host drivers
 // ===========================================================================
-int sweep_grid(const Plan* plan, const void* kernel, int block, int which) {
+int sweep_grid(const Plan* plan, const void* kernel, int block, int smem) {
   int per_sm = plan->p.blocks_per_sm;
-  if (per_sm <= 0) {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0);
-    per_sm = occ > 0 ? occ : 1;
-  }
-  (void)which;
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, (size_t)smem);
+  if (occ < 1) occ = 1;
+  if (per_sm <= 0 || per_sm > occ) per_sm = occ;
   int64_t need = (plan->ly.nw * 32 + block - 1) / block;
   int64_t g = (int64_t)plan->num_sms * per_sm;
   if (g > need) g = need;

@@ -32,7 +32,7 @@ struct Plan {
   int64_t n = 0;
   int32_t nb = 0;
   Tuning tune[16];
-  int variant[16] = {};  // launch variant per sweep (index into the pass's MB0..MB2)
+  int variant[16] = {};  // launch variant per sweep: v % 3 -> MB0..MB2, v >= 3 staged ring
   // instrumentation
   long long launches = 0;
   bool timing = false;
@@ -78,7 +78,7 @@ crk_status adjoint_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const
                         int recompute);
 
 // persistent grid size for a sweep kernel
-int sweep_grid(const Plan* plan, const void* kernel, int block, int which);
+int sweep_grid(const Plan* plan, const void* kernel, int block, int smem);
 
 }  // namespace crk
 

@@ -48,13 +48,81 @@ inline Common make_common(const Plan* plan, char* ws) {
   return c;
 }
 
+// ---------------------------------------------------------------------------
+// Asynchronous 16-byte global -> shared copies (cp.async, cached in L1).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Staging ring of a sweep whose pass sets STAGED: every thread owns two slots
+// of SV 16-byte vectors each, laid out [slot][vector][thread] so that the
+// threads of a warp touch consecutive 16-byte words (no bank conflicts).  The
+// neighbor record of list entry k+1 is copied into one slot while the pair of
+// entry k is evaluated from the other, so the gather latency overlaps the
+// arithmetic instead of stalling it.  Each thread reads back only its own
+// slots, and every value it reads is consumed before the slot is refilled.
+template <class P> struct Stage {
+  using R = typename P::Real;
+  static constexpr int V0 = P::SW0 * (int)sizeof(R) / 16;  // vectors of source 0
+  static constexpr int V1 = P::SW1 * (int)sizeof(R) / 16;  // vectors of source 1
+  static constexpr int SV = V0 + V1;
+  static constexpr size_t bytes = (size_t)2 * SV * P::BLOCK * 16;
+  __device__ static void issue(const typename P::Args& a, float4* ring, int slot, uint32_t j) {
+    const int t = threadIdx.x;
+    const float4* g0 = reinterpret_cast<const float4*>(P::src0(a)) + (size_t)j * V0;
+#pragma unroll
+    for (int v = 0; v < V0; ++v) cp_async16(&ring[(slot * SV + v) * P::BLOCK + t], g0 + v);
+    if constexpr (V1 > 0) {
+      const float4* g1 = reinterpret_cast<const float4*>(P::src1(a)) + (size_t)j * V1;
+#pragma unroll
+      for (int v = 0; v < V1; ++v)
+        cp_async16(&ring[(slot * SV + V0 + v) * P::BLOCK + t], g1 + v);
+    }
+  }
+  __device__ static void read(const float4* ring, int slot, R* r0, R* r1) {
+    const int t = threadIdx.x;
+    float4* o0 = reinterpret_cast<float4*>(r0);
+#pragma unroll
+    for (int v = 0; v < V0; ++v) o0[v] = ring[(slot * SV + v) * P::BLOCK + t];
+    if constexpr (V1 > 0) {
+      float4* o1 = reinterpret_cast<float4*>(r1);
+#pragma unroll
+      for (int v = 0; v < V1; ++v) o1[v] = ring[(slot * SV + V0 + v) * P::BLOCK + t];
+    }
+  }
+};
+
+// Neighbor record(s) of j straight from global memory (the unstaged path).
+template <class P>
+__device__ __forceinline__ void load_sources(const typename P::Args& a, uint32_t j,
+                                             typename P::Real* r0, typename P::Real* r1) {
+  load_rec<P::SW0>(P::src0(a), j, r0);
+  if constexpr (P::SW1 > 0) load_rec<P::SW1>(P::src1(a), j, r1);
+}
+template <class P>
+__device__ __forceinline__ void prefetch_sources(const typename P::Args& a, uint32_t j) {
+  prefetch_record(P::src0(a), j, P::SW0 * (int)sizeof(typename P::Real));
+  if constexpr (P::SW1 > 0)
+    prefetch_record(P::src1(a), j, P::SW1 * (int)sizeof(typename P::Real));
+}
+
 // Persistent sweep: warps pull 32-particle work items from an atomic queue.
-// MINB (minimum resident blocks per SM) sets the register cap; each pass is
-// compiled for three values and the autotuner picks one per plan.
-template <class P, int MINB>
+// MINB (minimum resident blocks per SM) sets the register cap and STG routes
+// the neighbor records through the shared-memory ring; each pass is compiled
+// for three MINB values with and without the ring and the autotuner picks one
+// of the six per plan.
+template <class P, int MINB, bool STG>
 __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args a) {
   const int lane = threadIdx.x & 31;
   int32_t* q = &a.c.hdr->queue[P::QUEUE];
+  extern __shared__ float4 ring[];
   for (;;) {
     int w = 0;
     if (lane == 0) w = atomicAdd(q, 1);
@@ -70,14 +138,46 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
       ls = P::GATHER ? 0 : a.c.cnt_s[s];
     }
     const uint32_t* col = a.c.ell + (int64_t)w * a.c.cap_pp * 32 + lane;
-    if (P::GATHER) {
+    using Real = typename P::Real;
+    if constexpr (STG) {
+      // union list (gather part, then scatter-only part) through the ring
+      const int tot = lg + ls;
+      const int wmax = __reduce_max_sync(kFull, tot);
+      auto entry = [&](int k) -> uint32_t {
+        const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
+        return __ldg(col + slot * 32);
+      };
+      uint32_t e_next = tot > 0 ? entry(0) : 0u;
+      if (tot > 0) Stage<P>::issue(a, ring, 0, e_next & kIdxMask);
+      cp_async_commit();
+      uint32_t e_after = tot > 1 ? entry(1) : 0u;
+      for (int k = 0; k < wmax; ++k) {
+        const uint32_t e = e_next;
+        e_next = e_after;
+        if (k + 1 < tot) Stage<P>::issue(a, ring, (k + 1) & 1, e_next & kIdxMask);
+        cp_async_commit();
+        e_after = k + 2 < tot ? entry(k + 2) : 0u;
+        cp_async_wait<1>();
+        if (k < tot) {
+          Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
+          Stage<P>::read(ring, k & 1, r0, r1);
+          P::pair_s(a, st, r0, r1, e & kIdxMask, e);
+        }
+      }
+      cp_async_wait<0>();
+    } else if (P::GATHER) {
       // gather part only: the same row of every lane is one 128-byte line
       const int wg = a.c.wlen_g[w];
       const int pf = a.c.pf;
       for (int k = 0; k < wg; ++k) {
-        if (pf && k + pf < lg) P::prefetch(a, __ldg(col + (int64_t)(k + pf) * 32) & kIdxMask);
+        if (pf && k + pf < lg)
+          prefetch_sources<P>(a, __ldg(col + (int64_t)(k + pf) * 32) & kIdxMask);
         const uint32_t e = __ldg(col + (int64_t)k * 32);
-        if (k < lg) P::pair(a, st, e & kIdxMask, e);
+        if (k < lg) {
+          Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
+          load_sources<P>(a, e & kIdxMask, r0, r1);
+          P::pair_s(a, st, r0, r1, e & kIdxMask, e);
+        }
       }
     } else {
       // gather part then scatter-only part as one list per lane, so the warp
@@ -90,12 +190,14 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
         if (pf && k + pf < tot) {
           const int kp = k + pf;
           const int64_t sp = kp < lg ? kp : a.c.cap_pp - 1 - (kp - lg);
-          P::prefetch(a, __ldg(col + sp * 32) & kIdxMask);
+          prefetch_sources<P>(a, __ldg(col + sp * 32) & kIdxMask);
         }
         if (k < tot) {
           const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
           const uint32_t e = __ldg(col + slot * 32);
-          P::pair(a, st, e & kIdxMask, e);
+          Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
+          load_sources<P>(a, e & kIdxMask, r0, r1);
+          P::pair_s(a, st, r0, r1, e & kIdxMask, e);
         }
       }
     }
@@ -310,20 +412,29 @@ template <class R> struct PairC2 {
   }
 };
 
+template <class P, int MB, bool STG>
+void launch_variant(Plan* plan, cudaStream_t st, const typename P::Args& a) {
+  const size_t smem = STG ? Stage<P>::bytes : 0;
+  const void* fn = (const void*)k_sweep<P, MB, STG>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int grid = sweep_grid(plan, fn, P::BLOCK, (int)smem);
+  k_sweep<P, MB, STG><<<grid, P::BLOCK, smem, st>>>(a);
+}
+
+// Variant v of a sweep: v % 3 picks the resident-block count (MB0..MB2),
+// v >= 3 the shared-memory ring.
 template <class P>
 void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const char* name) {
-  const int block = P::BLOCK;
   const int v = plan->variant[P::QUEUE];
   Phase ph(plan, st, name, 1);
-  if (v == 1) {
-    const int grid = sweep_grid(plan, (const void*)k_sweep<P, P::MB1>, block, P::QUEUE);
-    k_sweep<P, P::MB1><<<grid, block, 0, st>>>(a);
-  } else if (v == 2) {
-    const int grid = sweep_grid(plan, (const void*)k_sweep<P, P::MB2>, block, P::QUEUE);
-    k_sweep<P, P::MB2><<<grid, block, 0, st>>>(a);
-  } else {
-    const int grid = sweep_grid(plan, (const void*)k_sweep<P, P::MB0>, block, P::QUEUE);
-    k_sweep<P, P::MB0><<<grid, block, 0, st>>>(a);
+  switch (v) {
+    case 1: launch_variant<P, P::MB1, false>(plan, st, a); break;
+    case 2: launch_variant<P, P::MB2, false>(plan, st, a); break;
+    case 3: launch_variant<P, P::MB0, true>(plan, st, a); break;
+    case 4: launch_variant<P, P::MB1, true>(plan, st, a); break;
+    case 5: launch_variant<P, P::MB2, true>(plan, st, a); break;
+    default: launch_variant<P, P::MB0, false>(plan, st, a); break;
   }
 }
 
