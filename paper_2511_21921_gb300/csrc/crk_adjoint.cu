@@ -15,22 +15,6 @@
 
 namespace crk {
 
-// record layouts of the reverse sweeps (words of R per particle)
-template <class R> struct ARec {
-  static constexpr int XW = Prec<R>::XW;
-  static constexpr int VEC = Prec<R>::VEC;
-  // c1^T: x, ih, V, m, v[3], C[16], Nbar, Dbar, gvbar[9]
-  static constexpr int A1_IH = XW, A1_V = XW + 1, A1_M = XW + 2, A1_VEL = XW + 3, A1_C = XW + 6,
-                       A1_NB = XW + 22, A1_DB = XW + 23, A1_GVB = XW + 24,
-                       A1 = round_up(XW + 33, VEC);
-  // b2^T: x, ih, V, mbar[29]
-  static constexpr int A2_IH = XW, A2_V = XW + 1, A2_MB = XW + 2, A2 = round_up(XW + 31, VEC);
-  // b1^T: x, ih, sbar, m
-  static constexpr int A3_IH = XW, A3_SB = XW + 1, A3_M = XW + 2, A3 = round_up(XW + 3, VEC);
-  // per-particle accumulators: xbar[3], vbar[3], hbar, ubar, Vbar
-  static constexpr int XB = 0, VB = 3, HB = 6, UB = 7, VVB = 8, ACC = 12;
-};
-
 // (1/r) dg/dr of the Wendland C4 kernel: -30 c_g / h^7 (1-q)^4  (smooth at r = 0)
 template <class R> __device__ __forceinline__ R wendland_gg(R r, R ih) {
   R q = r * ih;

@@ -73,10 +73,15 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.Ds = take(R * N);
   // adjoint scratch (records of the reverse sweeps, per-particle accumulators)
   L.adj_ab = take(R * 4 * N);
-  L.adj_rec1 = take(R * 40 * N);
-  L.adj_rec2 = take(R * 40 * N);
-  L.adj_rec3 = take(R * 12 * N);
-  L.adj_acc = take(R * 12 * N);
+  const bool f64 = p.precision == CRK_FP64;
+  const size_t A1 = f64 ? ARec<double>::A1 : ARec<float>::A1;
+  const size_t A2 = f64 ? ARec<double>::A2 : ARec<float>::A2;
+  const size_t A3 = f64 ? ARec<double>::A3 : ARec<float>::A3;
+  const size_t ACC = f64 ? ARec<double>::ACC : ARec<float>::ACC;
+  L.adj_rec1 = take(R * A1 * N);
+  L.adj_rec2 = take(R * A2 * N);
+  L.adj_rec3 = take(R * A3 * N);
+  L.adj_acc = take(R * ACC * N);
   L.adj_cbar = take(R * 16 * N);
   L.tune_out = take(R * 12 * N);  // outputs of the autotuner's trial runs
   L.total = o;

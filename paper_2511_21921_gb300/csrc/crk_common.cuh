@@ -49,14 +49,17 @@ __device__ __forceinline__ void set_status(DevHeader* h, int code) {
 // pairs (6 words); double records carry them as plain doubles (3 words).
 // ---------------------------------------------------------------------------
 template <class R> struct Prec;
+// Records are padded to whole 32-byte words so that a neighbor record is
+// fetched with 256-bit loads (half the load instructions, and so half the L1
+// requests, of 128-bit loads for the same bytes).
 template <> struct Prec<float> {
   static constexpr int XW = 6;      // words of position per record
-  static constexpr int VEC = 4;     // words per vector load (float4)
+  static constexpr int VEC = 8;     // words per 256-bit load
   using V4 = float4;
 };
 template <> struct Prec<double> {
   static constexpr int XW = 3;
-  static constexpr int VEC = 2;     // double2
+  static constexpr int VEC = 4;     // words per 256-bit load
   using V4 = double2;
 };
 
@@ -71,7 +74,8 @@ template <class R> struct Rec {
   // b2 (moments): x, V
   static constexpr int B2_V = XW, B2 = round_up(XW + 1, VEC);
   // c1 (density, grad v): x, V, m, v[3]
-  static constexpr int C1_V = XW, C1_M = XW + 1, C1_VEL = XW + 2, C1 = round_up(XW + 5, VEC);
+  // (48 bytes in float: three 128-bit loads beat two 256-bit loads of a padded 64)
+  static constexpr int C1_V = XW, C1_M = XW + 1, C1_VEL = XW + 2, C1 = round_up(XW + 5, VEC / 2);
   // c2 (rates): x, ih, V, P, qa, qb, flag, v[3], A, B[3], dA[3], dB[9], gv[9]
   static constexpr int C2_IH = XW, C2_V = XW + 1, C2_P = XW + 2, C2_QA = XW + 3,
                        C2_QB = XW + 4, C2_FLAG = XW + 5, C2_VEL = XW + 6, C2_A = XW + 9,
@@ -79,23 +83,65 @@ template <class R> struct Rec {
                        C2 = round_up(XW + 34, VEC);
 };
 
-// vectorised load of a record of NW words (NW a multiple of the vector width)
+// Records of the reverse sweeps (adjoint), same conventions as Rec.
+template <class R> struct ARec {
+  static constexpr int XW = Prec<R>::XW;
+  static constexpr int VEC = Prec<R>::VEC;
+  // c1^T: x, ih, V, m, v[3], C[16], Nbar, Dbar, gvbar[9]
+  static constexpr int A1_IH = XW, A1_V = XW + 1, A1_M = XW + 2, A1_VEL = XW + 3, A1_C = XW + 6,
+                       A1_NB = XW + 22, A1_DB = XW + 23, A1_GVB = XW + 24,
+                       A1 = round_up(XW + 33, VEC);
+  // b2^T: x, ih, V, mbar[29]
+  static constexpr int A2_IH = XW, A2_V = XW + 1, A2_MB = XW + 2, A2 = round_up(XW + 31, VEC);
+  // b1^T: x, ih, sbar, m
+  static constexpr int A3_IH = XW, A3_SB = XW + 1, A3_M = XW + 2, A3 = round_up(XW + 3, VEC / 2);
+  // per-particle accumulators: xbar[3], vbar[3], hbar, ubar, Vbar
+  static constexpr int XB = 0, VB = 3, HB = 6, UB = 7, VVB = 8, ACC = 12;
+};
+
+// vectorised load of a record of NW words (NW a multiple of 4 floats or 2
+// doubles); 256-bit loads when NW fills whole 32-byte words (the record must
+// then start on a 32-byte boundary, which every record array in the
+// workspace does), 128-bit loads otherwise.
 template <int NW>
 __device__ __forceinline__ void load_rec(const float* __restrict__ base, int64_t s, float* out) {
-  const float4* p = reinterpret_cast<const float4*>(base + s * NW);
+  if constexpr (NW % 8 == 0) {
+    const float* p = base + s * NW;
 #pragma unroll
-  for (int k = 0; k < NW / 4; ++k) {
-    float4 t = __ldg(p + k);
-    out[4 * k + 0] = t.x; out[4 * k + 1] = t.y; out[4 * k + 2] = t.z; out[4 * k + 3] = t.w;
+    for (int k = 0; k < NW / 8; ++k) {
+      float* o = out + 8 * k;
+      asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+          : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]),
+            "=f"(o[7])
+          : "l"(p + 8 * k));
+    }
+  } else {
+    const float4* p = reinterpret_cast<const float4*>(base + s * NW);
+#pragma unroll
+    for (int k = 0; k < NW / 4; ++k) {
+      float4 t = __ldg(p + k);
+      out[4 * k + 0] = t.x; out[4 * k + 1] = t.y; out[4 * k + 2] = t.z; out[4 * k + 3] = t.w;
+    }
   }
 }
 template <int NW>
 __device__ __forceinline__ void load_rec(const double* __restrict__ base, int64_t s, double* out) {
-  const double2* p = reinterpret_cast<const double2*>(base + s * NW);
+  if constexpr (NW % 4 == 0) {
+    const double* p = base + s * NW;
 #pragma unroll
-  for (int k = 0; k < NW / 2; ++k) {
-    double2 t = __ldg(p + k);
-    out[2 * k + 0] = t.x; out[2 * k + 1] = t.y;
+    for (int k = 0; k < NW / 4; ++k) {
+      double* o = out + 4 * k;
+      asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+          : "=d"(o[0]), "=d"(o[1]), "=d"(o[2]), "=d"(o[3])
+          : "l"(p + 4 * k));
+    }
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(base + s * NW);
+#pragma unroll
+    for (int k = 0; k < NW / 2; ++k) {
+      double2 t = __ldg(p + k);
+      out[2 * k + 0] = t.x; out[2 * k + 1] = t.y;
+    }
   }
 }
 template <int NW>
