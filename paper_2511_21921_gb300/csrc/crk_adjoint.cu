@@ -232,7 +232,7 @@ __global__ void k_adj_prep(const R* __restrict__ gdv, const R* __restrict__ gdu,
 template <class R> struct PassA2 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
-  static constexpr int MB0 = 1, MB1 = 8, MB2 = 10;  // resident-block variants
+  static constexpr int MB0 = 1, MB1 = 6, MB2 = 8;  // resident-block variants
   static constexpr int QUEUE = Q_A_C2;
   using Real = R;
   static constexpr int SW0 = Rec<R>::C2, SW1 = 4;  // words staged per neighbor
@@ -490,7 +490,7 @@ template <class R> struct PassA2 {
 template <class R> struct PassA1 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
-  static constexpr int MB0 = 1, MB1 = 8, MB2 = 10;  // resident-block variants
+  static constexpr int MB0 = 1, MB1 = 6, MB2 = 8;  // resident-block variants
   static constexpr int QUEUE = Q_A_C1;
   using Real = R;
   static constexpr int SW0 = ARec<R>::A1, SW1 = 0;  // words staged per neighbor
