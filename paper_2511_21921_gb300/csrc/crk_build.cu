@@ -622,18 +622,28 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
         __syncwarp();
         if (act) {
           if (fast) {
-            // float predicate on the nearest images: no per-pair wrap
+            // float predicate on the nearest images: no per-pair wrap.  All
+            // 32 staged candidates are tested branch-free into two bit
+            // masks; only the hits (a few per stage) are then emitted, in
+            // candidate order.
             const float hi2f = (float)hi * (float)hi;
-#pragma unroll 8
+            uint32_t mg = 0u, msc = 0u;
+#pragma unroll
             for (int k = 0; k < 32; ++k) {
               const float4 t = s4[wib][k];
               const float dx = p[0] - t.x, dy = p[1] - t.y, dz = p[2] - t.z;
               const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-              const bool g = r2 < hi2f;
-              const bool sc = r2 < t.w;
-              if (!(g || sc)) continue;
+              mg |= (r2 < hi2f ? 1u : 0u) << k;
+              msc |= (r2 < t.w ? 1u : 0u) << k;
+            }
+            uint32_t hit = mg | msc;
+            while (hit) {
+              const int k = __ffs(hit) - 1;
+              hit &= hit - 1u;
               const int32_t j = sj[wib][k];
               if (j == s) continue;
+              const bool g = (mg >> k) & 1u;
+              const bool sc = (msc >> k) & 1u;
               const uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
               if (kg + ks < cap_pp) {
                 const int64_t kk = g ? kg : cap_pp - 1 - ks;
