@@ -20,8 +20,8 @@
  *                      subgrid calibration of Sec. 3 a gradient).
  *   crk_hdot, crk_kick, crk_kick_refined, crk_drift
  *                   -- the time step around the rates: smoothing-length rate
- *                      and exponential drifts (App. B.1), kick-drift-kick with
- *                      refined kicks and parabolic passive drifts (App. B.2).
+ *                      and exponential drifts (App. A.3), kick-drift-kick with
+ *                      refined kicks and parabolic passive drifts (App. A.4).
  *
  * Conventions shared by every entry point:
  *  - Device pointers are owned by the caller; the library never allocates
@@ -141,7 +141,7 @@ crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void
                        const void* g_dvdt, const void* g_dudt, void* g_x, void* g_v, void* g_u,
                        void* g_h, int32_t recompute);
 
-/* ---- Time step around the rates (App. B.1 and B.2) -------------------------
+/* ---- Time step around the rates (App. A.3 and A.4) -------------------------
  * A kick-drift-kick step is: crk_kick (half kick with the rates of the last
  * evaluation), crk_drift (positions, smoothing lengths), crk_cell_build,
  * crk_moments, crk_rates at the new positions, crk_hdot, crk_kick (second
@@ -149,7 +149,7 @@ crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void
  * neither read nor write the workspace except crk_hdot, which reads it.
  * Element types follow params.precision as everywhere else. */
 
-/* (e) Smoothing-length rate (App. B.1, Smoothing Length Integration):
+/* (e) Smoothing-length rate (App. A.3, Smoothing Length Integration):
  *   hdot_i = (h^T_i - h_i) / dt_a + h_i (div v)_i / 3,
  *   h^T_i  = h_i (1 - lambda + lambda Delta_N),  Delta_N = n_h V_i^(1/3) / h_i,
  * with V_i the volume of the last crk_moments, (div v)_i the trace of the
@@ -162,9 +162,9 @@ crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void
 crk_status crk_hdot(crk_plan* plan, crk_stream_t stream, void* ws, double dt_a, double lambda,
                     double n_h, void* hdot_out, void* hrate_out, void* div_out);
 
-/* (f) Kick (App. B.2, K): v_out = v0 + dt a and, when u_out is given,
+/* (f) Kick (App. A.4, K): v_out = v0 + dt a and, when u_out is given,
  * u_out = u0 + dt dudt.  dt is the kick length (dt_a/2 for a half kick; the
- * refined first half kick of App. B.2 is this call from v0 with dt_b/2).
+ * refined first half kick of App. A.4 is this call from v0 with dt_b/2).
  * active: optional device uint8[n]; particles with active[i] == 0 keep v0 (and
  * u0).  v0, a, v_out: device real[3][n]; u0, dudt, u_out: device real[n].
  * Outputs may alias inputs (in-place kicks).  n <= the plan's n_max. */
@@ -172,7 +172,7 @@ crk_status crk_kick(crk_plan* plan, crk_stream_t stream, int64_t n, double dt,
                     const uint8_t* active, const void* v0, const void* a, void* v_out,
                     const void* u0, const void* dudt, void* u_out);
 
-/* (g) Completion of a refined step (App. B.2, Adaptive Kick Corrections):
+/* (g) Completion of a refined step (App. A.4, Adaptive Kick Corrections):
  *   v_out = v0 + a0 (dt_b - dt_c) + (a0 + a1) dt_c / 2
  * (and likewise u from u0, du0, du1 when u_out is given): constant a0 until
  * the last dt_c of the refined interval dt_b, then a plain kick-drift-kick
@@ -182,7 +182,7 @@ crk_status crk_kick_refined(crk_plan* plan, crk_stream_t stream, int64_t n, doub
                             const void* a1, void* v_out, const void* u0, const void* du0,
                             const void* du1, void* u_out);
 
-/* (h) Drift by dt >= 0 (App. B.2, D), in place, and the drifts of App. B.1.
+/* (h) Drift by dt >= 0 (App. A.4, D), in place, and the drifts of App. A.3.
  *   x: device double[3][n], updated in double as x + v dt and wrapped into the
  *      particle's box [0, L) (box_off/box_L as for crk_cell_build); a particle
  *      that moves more than one box side is left outside and the next

@@ -6,16 +6,16 @@ operation per line where the GPU path must reproduce the rounding order.
 
 What it computes (paper sections and equations):
 
-* ``hdot``            -- smoothing-length rate of App. B.1 (Smoothing Length
+* ``hdot``            -- smoothing-length rate of App. A.3 (Smoothing Length
   Integration): the Thacker estimate h^T = h (1 - lambda + lambda Delta_N) with
   Delta_N^3 = V n_h^3 / h^3, its rate (h^T - h)/dt_a, plus the continuity rate
   h (div v)/3.
-* ``drift_h``, ``drift_passive`` -- the exponential drift of App. B.1:
+* ``drift_h``, ``drift_passive`` -- the exponential drift of App. A.3:
   h <- h exp[(hdot/h) dt], V <- (h/n_h)^3, rho <- rho exp[-(div v) dt].
-* ``kick``            -- one kick of the KDK update of App. B.2 (K: v + a dt/2).
-* ``kick_refined``    -- the piecewise-constant completion of App. B.2 when the
+* ``kick``            -- one kick of the KDK update of App. A.4 (K: v + a dt/2).
+* ``kick_refined``    -- the piecewise-constant completion of App. A.4 when the
   step is refined from dt_b to dt_c: v0 + a0 (dt_b - dt_c) + (a0 + a1) dt_c / 2.
-* ``drift``           -- the drift of App. B.2, with the parabolic passive
+* ``drift``           -- the drift of App. A.4, with the parabolic passive
   trajectory: the velocity used over sub-step j is
   v_half + a0 [t_elapse + (dt_j - dt_a)/2], and positions accumulate in double.
 * ``kdk_step``        -- one global KDK step around ``oracle.forward``.
@@ -40,7 +40,7 @@ from .oracle import forward
 
 
 def hdot(h, V, div, dt_a, lam, n_h):
-    """Smoothing-length rate (App. B.1).  Returns (hdot, hdot / h).
+    """Smoothing-length rate (App. A.3).  Returns (hdot, hdot / h).
 
     h, V, div: float64 arrays (n,); dt_a > 0 the active time step; lam the
     Thacker weight; n_h the target number of particles per kernel radius.
@@ -60,12 +60,12 @@ def hdot(h, V, div, dt_a, lam, n_h):
 
 
 def drift_h(h, hrate, dt):
-    """h exp[(hdot/h) dt] with the logarithmic rate held fixed (App. B.1)."""
+    """h exp[(hdot/h) dt] with the logarithmic rate held fixed (App. A.3)."""
     return np.asarray(h, np.float64) * np.exp(np.asarray(hrate, np.float64) * dt)
 
 
 def drift_passive(h_new, rho, div, dt, n_h):
-    """Passive volume and density after a drift (App. B.1):
+    """Passive volume and density after a drift (App. A.3):
     V = (h/n_h)^3 and rho exp(-div dt)."""
     q = np.asarray(h_new, np.float64) / n_h
     V = q * q * q
@@ -74,14 +74,14 @@ def drift_passive(h_new, rho, div, dt, n_h):
 
 
 def kick(v0, a, dt):
-    """v0 + dt a (App. B.2, K).  dt is the kick length (dt_a / 2 for a half kick)."""
+    """v0 + dt a (App. A.4, K).  dt is the kick length (dt_a / 2 for a half kick)."""
     v0 = np.asarray(v0, np.float64)
     t = dt * np.asarray(a, np.float64)
     return v0 + t
 
 
 def kick_refined(v0, a0, a1, dt_b, dt_c):
-    """Completion of a refined step (App. B.2):
+    """Completion of a refined step (App. A.4):
     v0 + a0 (dt_b - dt_c) + (a0 + a1) dt_c / 2."""
     v0 = np.asarray(v0, np.float64)
     a0 = np.asarray(a0, np.float64)
@@ -105,7 +105,7 @@ def wrap(y, L):
 
 
 def drift(x, v_half, dt, L, a0=None, dt_a=None, t_elapse=None):
-    """Positions after one drift of length dt (App. B.2), in float64.
+    """Positions after one drift of length dt (App. A.4), in float64.
 
     x: (3, n) float64; v_half: (3, n) stored half-step velocity.  Without a0
     the drift is linear in v_half.  With a0, particle i drifts with the local
@@ -137,8 +137,8 @@ def kdk_init(x, v, u, h, m, L, dt_a, lam, n_h, params=None):
 
 
 def kdk_step(x, v, u, h, m, L, d0, dt, lam, n_h, params=None):
-    """One global kick-drift-kick step of length dt (App. B.2) with the
-    smoothing-length drift of App. B.1.
+    """One global kick-drift-kick step of length dt (App. A.4) with the
+    smoothing-length drift of App. A.3.
 
     d0: the derivatives at the start ({"a", "du", "hrate"}, from ``kdk_init`` or
     the previous step).  Returns (x1, v1, u1, h1, d1) with d1 the derivatives at

@@ -1,14 +1,14 @@
 // crk_step.cu -- the time step around the rates: smoothing-length rate,
 // kicks and drift.
 //
-//   crk_hdot          App. B.1: hdot = (h^T - h)/dt_a + h (div v)/3 with the
+//   crk_hdot          App. A.3: hdot = (h^T - h)/dt_a + h (div v)/3 with the
 //                     Thacker estimate h^T = h (1 - lambda + lambda Delta_N),
 //                     Delta_N = n_h V^(1/3) / h, from the volume and velocity
 //                     gradient the last crk_moments / crk_rates left in ws.
-//   crk_kick          App. B.2 (K): v0 + dt a (and u0 + dt du/dt).
-//   crk_kick_refined  App. B.2: v0 + a0 (dt_b - dt_c) + (a0 + a1) dt_c / 2.
-//   crk_drift         App. B.2 (D) with the parabolic passive trajectory, and
-//                     App. B.1's h exp[(hdot/h) dt], V = (h/n_h)^3,
+//   crk_kick          App. A.4 (K): v0 + dt a (and u0 + dt du/dt).
+//   crk_kick_refined  App. A.4: v0 + a0 (dt_b - dt_c) + (a0 + a1) dt_c / 2.
+//   crk_drift         App. A.4 (D) with the parabolic passive trajectory, and
+//                     App. A.3's h exp[(hdot/h) dt], V = (h/n_h)^3,
 //                     rho exp(-div dt).
 //
 // Every kernel is one pass over the particles (HBM-bound, a few tens of bytes

@@ -69,7 +69,7 @@ def test_kick_and_refined_kick(precision):
     e = I.kick(v0, a0, dt)
     sc = np.abs(v0) + np.abs(dt * a0)
     assert np.max(np.abs(got[:, on] - e[:, on]) / sc[:, on]) <= tol
-    # refined completion (App. B.2) for a range of dt_c
+    # refined completion (App. A.4) for a range of dt_c
     for dt_c in (dt, 0.4 * dt, 0.0):
         vo, uo = s.kick_refined(dt, dt_c, tv0, ta0, ta1, tu0, tdu0, tdu1,
                                 v_out=torch.empty_like(tv0), u_out=torch.empty_like(tu0))
@@ -205,7 +205,7 @@ def _min_image(a, L=1.0):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_kdk_steps_against_oracle(precision):
-    """Three global kick-drift-kick steps (App. B.1 and B.2) on the 32^3
+    """Three global kick-drift-kick steps (App. A.3 and B.2) on the 32^3
     lognormal box: state and derivatives against the oracle's steps."""
     d = synth.load("lognormal32")
     n = d["h"].shape[0]

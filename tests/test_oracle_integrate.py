@@ -25,7 +25,7 @@ NH = (3.0 * 100 / (4.0 * np.pi)) ** (1.0 / 3.0)   # the synthetic workloads' ~10
 
 def test_kdk_harmonic_oscillator_recurrence():
     """KDK from the oracle's kick and drift on a = -w^2 (x - c): positions obey
-    x_{n+1} - 2 x_n + x_{n-1} = -(w dt)^2 (x_n - c) (App. B.2 is leapfrog), and
+    x_{n+1} - 2 x_n + x_{n-1} = -(w dt)^2 (x_n - c) (App. A.4 is leapfrog), and
     the first step is x0 + v0 dt - (w dt)^2 (x0 - c) / 2."""
     w, dt, c, L = 1.3, 0.07, 500.0, 1000.0
     rng = np.random.default_rng(0)
@@ -50,7 +50,7 @@ def test_kdk_harmonic_oscillator_recurrence():
 
 def test_passive_parabolic_drift_is_exact_parabola():
     """Sub-steps of a passive particle with the local half-step velocity of
-    App. B.2 trace x0 + v0 t + a t^2 / 2 exactly under constant acceleration,
+    App. A.4 trace x0 + v0 t + a t^2 / 2 exactly under constant acceleration,
     at every sub-step end, for any partition of the active interval."""
     rng = np.random.default_rng(1)
     n, L = 7, 1e6
@@ -67,7 +67,7 @@ def test_passive_parabolic_drift_is_exact_parabola():
         x = I.drift(x, vh, dtj, L, a0=a, dt_a=np.full(n, dt_a), t_elapse=np.full(n, te))
         te += dtj
         assert np.allclose(x, x0 + v0 * te + 0.5 * a * te * te, rtol=0, atol=1e-9)
-    # with no refinement the end point equals the linear drift with v_half (App. B.2)
+    # with no refinement the end point equals the linear drift with v_half (App. A.4)
     assert np.allclose(x, I.drift(x0, vh, dt_a, L), rtol=0, atol=1e-9)
     # an active particle (dt_a = dt, no elapsed time) drifts linearly
     assert np.array_equal(I.drift(x0, vh, 0.1, L, a0=a), I.drift(x0, vh, 0.1, L))
@@ -76,7 +76,7 @@ def test_passive_parabolic_drift_is_exact_parabola():
 def test_refined_kick_integrates_piecewise_acceleration():
     """v1 of the refined completion equals v0 plus the exact integral of an
     acceleration held at a0 over dt_b - dt_c and linear from a0 to a1 over the
-    last dt_c (App. B.2); dt_c = dt_b is the plain KDK, dt_c = 0 constant a0."""
+    last dt_c (App. A.4); dt_c = dt_b is the plain KDK, dt_c = 0 constant a0."""
     rng = np.random.default_rng(2)
     v0, a0, a1 = rng.normal(size=(3, 3, 4))
     dt_b = 0.3
@@ -99,7 +99,7 @@ def test_refined_kick_integrates_piecewise_acceleration():
 
 
 def test_delta_n_is_neighbor_count_ratio():
-    """Delta_N^3 = N_res / N_i (App. B.1): N_res = (4 pi/3) n_h^3 is the target
+    """Delta_N^3 = N_res / N_i (App. A.3): N_res = (4 pi/3) n_h^3 is the target
     count (268 for the paper's gas n_h = 4, App. A.2) and N_i = (4 pi/3) h^3 / V
     the count a particle of volume V sees within h.  With lambda = 1 and no
     divergence, one active step takes h exactly to the target radius."""
@@ -130,7 +130,7 @@ def test_delta_n_is_neighbor_count_ratio():
 def test_passive_drift_conserves_mass_and_composes():
     """With h at its target (Delta_N = 1) the passive update V = (h/n_h)^3,
     rho exp(-div dt) keeps V rho (a particle's mass) fixed, and drifts over
-    sub-steps compose to one drift over their sum (App. B.1)."""
+    sub-steps compose to one drift over their sum (App. A.3)."""
     rng = np.random.default_rng(4)
     n = 64
     nh = NH
@@ -164,7 +164,7 @@ def test_wrap_stays_in_box_and_is_congruent():
 
 
 def test_kdk_galilean_invariance_on_lattice():
-    """A perfect lattice moving with one velocity feels no force (App. B.2
+    """A perfect lattice moving with one velocity feels no force (App. A.4
     KDK around the rates): positions advance by v t modulo the box, velocities
     and energies stay put."""
     n_side = 10
@@ -194,7 +194,7 @@ def test_kdk_galilean_invariance_on_lattice():
 def test_kdk_conserves_momentum_and_converges_in_energy():
     """Pairwise-antisymmetric forces keep sum m v fixed through kicks and drifts;
     the compatible energy update keeps E = sum m (v^2/2 + u) to an error that
-    shrinks with the step (Sec. 2.1, App. B.2)."""
+    shrinks with the step (Sec. 2.1, App. A.4)."""
     d = synth.lattice(12, seed=5, jitter=0.15, k_target=64)
     x, v, u, h, m = d["x"], d["v"], d["u"], d["h"], d["m"]
     p0 = (m * v).sum(axis=1)
