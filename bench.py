@@ -317,6 +317,7 @@ def run_ours(args, rank, world):
     }
     if args.hydro and world == 1 and "box_off" not in d:
         res["hydro_step"] = hydro_step(args, d, dev, flush)
+        res["cooling"] = cooling_leg(args, d, dev, flush)
     if args.fp64_compare and world == 1 and prec == "mixed":
         res["fp64_gpu"] = fp64_compare(args, d, dev)
         if res["fp64_gpu"]:
@@ -386,6 +387,49 @@ def hydro_step(args, d, dev, flush):
             "gather_pairs_first": pairs, "gather_pairs_last": st["gather_pairs"],
             "launches_per_step": launches, "device_status": status,
             "step": "kick+drift+build+moments+rates+hdot+kick (graph)"}
+
+
+def cooling_leg(args, d, dev, flush):
+    """Exact-integration cooling (Sec. 2.3.2) of the whole box over one step:
+    a 0.004 dex table over six decades holding the self-similar law
+    lam = A u^1.5 above an equilibrium and heating below it; rho from the
+    density of the box's own rates evaluation."""
+    import torch
+    from paper_2511_21921_gb300.solver import Solver
+    n = d["h"].shape[0]
+    prec = args.precision
+    dt_ = torch.float32 if prec == "mixed" else torch.float64
+    s = Solver(n, 1, prec, device=dev)
+    t = {"x": torch.tensor(d["x"], dtype=torch.float64, device=dev)}
+    for k in ("h", "m", "u"):
+        t[k] = torch.tensor(d[k], dtype=dt_, device=dev)
+    t["v"] = torch.tensor(d["v"], dtype=dt_, device=dev)
+    rho = s.forward(t["x"], t["h"], t["m"], t["v"], t["u"], want_rho=True)["rho"]
+    lu0, dex, K = -3.0, 0.004, 1501
+    un = 10.0 ** (lu0 + dex * np.arange(K))
+    A, H = 1.0, 0.5
+    lam = torch.tensor(A * un ** 1.5 - H, dtype=torch.float64, device=dev)
+    dt = 0.1 / float(rho.double().median())   # typical energies move by a few to tens of bins
+    out = torch.empty_like(t["u"])
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        s.cool(dt, rho, t["u"], lam, lu0, dex, out=out)
+    k_steps = max(3, min(args.steps, 20))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(k_steps)]
+    for k in range(k_steps):
+        flush.fill_(k & 0xff)
+        evs[k][0].record(stream)
+        s.cool(dt, rho, t["u"], lam, lu0, dex, out=out)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / k_steps
+    bins = np.abs(np.log10(out.double().cpu().numpy() / d["u"])) / dex
+    nbytes = 3 * n * (4 if prec == "mixed" else 8)
+    return {"ms": round(ms, 5), "particles_per_s": n / (ms * 1e-3),
+            "bytes_per_particle": nbytes // n, "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
+            "bins_walked_median": float(np.median(bins)), "bins_walked_max": float(bins.max()),
+            "table": "lam = u^1.5 - 0.5 over 1e-3..1e3, 0.004 dex", "dt_rho_median": 0.1}
 
 
 def fp64_compare(args, d, dev):

@@ -22,6 +22,8 @@
  *                   -- the time step around the rates: smoothing-length rate
  *                      and exponential drifts (App. A.3), kick-drift-kick with
  *                      refined kicks and parabolic passive drifts (App. A.4).
+ *   crk_cool_exact  -- exact integration of radiative cooling and heating over
+ *                      a step (Sec. 2.3.2).
  *
  * Conventions shared by every entry point:
  *  - Device pointers are owned by the caller; the library never allocates
@@ -202,6 +204,33 @@ crk_status crk_drift(crk_plan* plan, crk_stream_t stream, int64_t n, int32_t n_b
                      const void* v_half, const void* a0, const double* dt_a,
                      const double* t_elapse, void* h, const void* hrate, double n_h, void* V,
                      void* rho, const void* div);
+
+/* ---- Radiative cooling and heating (Sec. 2.3.2, Exact Integration) ----------
+ * The source function of du/dt = -Lambda(u; rho)/rho is tabulated as
+ * lam_k = Lambda(u_k)/rho^2 at n_nodes energies u_k = 10^(log10_u_min +
+ * k dlog10_u) (lam > 0 cools, lam < 0 heats; the rho^2 scaling is that of the
+ * self-similar power-law test of App. B) and interpolated with a power law in
+ * every bin (Eq. L). */
+typedef struct {
+  int32_t n_nodes;       /* >= 2 */
+  int32_t reserved;
+  double log10_u_min;    /* log10 of the first node */
+  double dlog10_u;       /* node spacing in dex, > 0 (the paper uses 0.004) */
+  const double* lambda;  /* device double[n_nodes], owned by the caller */
+} crk_cool_table;
+
+/* (i) Exact integration over a step dt >= 0 with rho held fixed (Eqs. intcool,
+ * Iu, Iinv): every particle walks the table bins from its own energy (the
+ * anchor u_a = u0) and inverts the power-law integral in the bin where rho dt
+ * runs out.  A bin whose edge values differ in sign holds the equilibrium: it
+ * is crossed at the constant rate max(|lam_k|, |lam_k+1|) and the energy stops
+ * at the linearly interpolated zero crossing.  The table ends are a floor and a
+ * ceiling; an energy outside [u_min, u_max] is returned unchanged.
+ * rho, u0, u1: device real[n] (u1 may alias u0); n <= the plan's n_max.
+ * One pass over the particles; no workspace. */
+crk_status crk_cool_exact(crk_plan* plan, crk_stream_t stream, int64_t n,
+                          const crk_cool_table* table, double dt, const void* rho,
+                          const void* u0, void* u1);
 
 /* Autotuner for the launch shapes of the eight neighbor sweeps (volume,
  * moments, density, rates and the four adjoint sweeps).  Each sweep is

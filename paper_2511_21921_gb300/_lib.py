@@ -41,6 +41,11 @@ class crk_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 24), ("ms", C.c_float)]
 
 
+class crk_cool_table(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("reserved", C.c_int32), ("log10_u_min", C.c_double),
+                ("dlog10_u", C.c_double), ("lambda_", C.c_void_p)]
+
+
 class CRKError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = int(code)
@@ -69,6 +74,8 @@ _SIGS = {
     "crk_autotune": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int32, _VP, _VP]),
     "crk_volume_static": (C.c_int, [_VP, C.c_int32, C.c_int64, C.c_double, C.c_double, _VP, _VP,
                                     _VP, _VP]),
+    "crk_cool_exact": (C.c_int, [_VP, _VP, C.c_int64, C.POINTER(crk_cool_table), C.c_double, _VP,
+                                 _VP, _VP]),
     "crk_hdot": (C.c_int, [_VP, _VP, _VP, C.c_double, C.c_double, C.c_double, _VP, _VP, _VP]),
     "crk_kick": (C.c_int, [_VP, _VP, C.c_int64, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "crk_kick_refined": (C.c_int, [_VP, _VP, C.c_int64, C.c_double, C.c_double, _VP, _VP, _VP,
@@ -225,6 +232,11 @@ def crk_drift(plan, stream, n, n_boxes, box_off, box_L, dt, x, v_half, a0=None, 
                             _VP(box_L), float(dt), _VP(x), _VP(v_half), _VP(a0), _VP(dt_a),
                             _VP(t_elapse), _VP(h), _VP(hrate), float(n_h), _VP(V), _VP(rho),
                             _VP(div))
+
+
+def crk_cool_exact(plan, stream, n, table: crk_cool_table, dt, rho, u0, u1) -> int:
+    return load().crk_cool_exact(_VP(plan), _VP(stream), int(n), C.byref(table), float(dt),
+                                 _VP(rho), _VP(u0), _VP(u1))
 
 
 SWEEPS = ("b1_volume", "b2_moments", "c1_density", "c2_rates", "adj_c2", "adj_c1", "adj_b2",

@@ -202,6 +202,18 @@ class Solver:
                             _ptr(rho), _ptr(div)), "crk_drift")
         return x
 
+    def cool(self, dt, rho, u, lam, log10_u_min, dlog10_u, out=None):
+        """Exact-integration cooling/heating over dt (lam: float64 device tensor
+        of Lambda(u_k)/rho^2 at the table nodes)."""
+        n = int(u.shape[0])
+        assert lam.dtype == torch.float64 and lam.is_cuda and lam.is_contiguous()
+        tab = L.crk_cool_table(int(lam.shape[0]), 0, float(log10_u_min), float(dlog10_u),
+                               lam.data_ptr())
+        out = torch.empty_like(u) if out is None else out
+        L.check(L.crk_cool_exact(self.plan, _stream(), n, tab, dt, rho.data_ptr(), u.data_ptr(),
+                                 out.data_ptr()), "crk_cool_exact")
+        return out
+
     def kdk_init(self, x, v, u, h, m, dt_a, lam, n_h, box_off=None, box_L=None, L_box=1.0):
         """Rates and smoothing-length rate at the start of the first step."""
         self.cell_build(x, h, box_off, box_L, L_box)
