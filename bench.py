@@ -318,6 +318,7 @@ def run_ours(args, rank, world):
     if args.hydro and world == 1 and "box_off" not in d:
         res["hydro_step"] = hydro_step(args, d, dev, flush)
         res["cooling"] = cooling_leg(args, d, dev, flush)
+        res["subgrid"] = subgrid_leg(args, d, dev, flush)
     if args.fp64_compare and world == 1 and prec == "mixed":
         res["fp64_gpu"] = fp64_compare(args, d, dev)
         if res["fp64_gpu"]:
@@ -430,6 +431,56 @@ def cooling_leg(args, d, dev, flush):
             "bytes_per_particle": nbytes // n, "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
             "bins_walked_median": float(np.median(bins)), "bins_walked_max": float(bins.max()),
             "table": "lam = u^1.5 - 0.5 over 1e-3..1e3, 0.004 dex", "dt_rho_median": 0.1}
+
+
+def subgrid_leg(args, d, dev, flush):
+    """Subgrid particles over the gas (App. A.2 Eq. Vsg; Eqs. windmetal,
+    starmetal, AGNE): 5 % of the gas count as star particles, half spawned on
+    gas positions and half at random points, h_s = 0.6 h of the local gas;
+    their scatter volumes and a two-component normalised deposit, timed after
+    one build + moments of the box."""
+    import torch
+    from paper_2511_21921_gb300.solver import Solver
+    n = d["h"].shape[0]
+    prec = args.precision
+    dt_ = torch.float32 if prec == "mixed" else torch.float64
+    rng = np.random.default_rng(11)
+    n_s = n // 20
+    pick = rng.choice(n, n_s // 2, replace=False)
+    xs = np.concatenate([d["x"][:, pick], rng.uniform(0, 1, (3, n_s - n_s // 2))], axis=1)
+    hs = np.concatenate([d["h"][pick], rng.uniform(0.5, 1.5, n_s - n_s // 2) *
+                         np.median(d["h"])]) * 0.6
+    s = Solver(n, 1, prec, device=dev)
+    t = {"x": torch.tensor(d["x"], dtype=torch.float64, device=dev),
+         "h": torch.tensor(d["h"], dtype=dt_, device=dev),
+         "m": torch.tensor(d["m"], dtype=dt_, device=dev)}
+    s.cell_build(t["x"], t["h"])
+    s.moments(t["m"])
+    xs_d = torch.tensor(xs, dtype=torch.float64, device=dev).contiguous()
+    hs_d = torch.tensor(hs, dtype=dt_, device=dev)
+    q = torch.ones((2, n_s), dtype=dt_, device=dev)
+    dq = torch.zeros((2, n), dtype=dt_, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, fn in (("volume", lambda: s.subgrid_volume(xs_d, hs_d, 2.25)),
+                     ("deposit", lambda: s.subgrid_deposit(xs_d, hs_d, q, dq=dq))):
+        for _ in range(3):
+            fn()
+        k_steps = max(3, min(args.steps, 20))
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k_steps)]
+        for k in range(k_steps):
+            flush.fill_(k & 0xff)
+            evs[k][0].record(stream)
+            fn()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / k_steps
+        res[name + "_ms"] = round(ms, 5)
+        res[name + "_per_s"] = n_s / (ms * 1e-3)
+    res["n_subgrid"] = n_s
+    res["device_status"] = s.poll()
+    return res
 
 
 def fp64_compare(args, d, dev):

@@ -24,6 +24,9 @@
  *                      refined kicks and parabolic passive drifts (App. A.4).
  *   crk_cool_exact  -- exact integration of radiative cooling and heating over
  *                      a step (Sec. 2.3.2).
+ *   crk_subgrid_volume, crk_subgrid_deposit
+ *                   -- subgrid particles over the gas: scatter volumes (App.
+ *                      A.2) and normalised kernel deposits (Secs. 2.5-2.7).
  *
  * Conventions shared by every entry point:
  *  - Device pointers are owned by the caller; the library never allocates
@@ -204,6 +207,37 @@ crk_status crk_drift(crk_plan* plan, crk_stream_t stream, int64_t n, int32_t n_b
                      const void* v_half, const void* a0, const double* dt_a,
                      const double* t_elapse, void* h, const void* hrate, double n_h, void* V,
                      void* rho, const void* div);
+
+/* ---- Subgrid particles over the gas (App. A.2; Secs. 2.5.3, 2.6.3, 2.7.4) -----
+ * Stars, winds and black holes interact with the gas of the last
+ * crk_cell_build through its bucket tree.  Subgrid arrays are in the caller's
+ * order: box_off_s: device int64[n_boxes+1] (same boxes, same order as the
+ * build), x_s: device double[3][n_s] inside their box, h_s: device real[n_s].
+ * One thread per subgrid particle; no workspace beyond the built one. */
+
+/* (j) Scatter volume (App. A.2, Eq. Vsg): V_s = 1 / (sum over gas j with
+ * r_sj < h_j of W(r_sj, h_j) + W(0, h_s)); optional h_out = n_h V_s^(1/3)
+ * (the smoothing length the volume determines; n_h = 2.25 for stars and black
+ * holes, 4 for winds in the paper).  V_out, h_out: device real[n_s]. */
+crk_status crk_subgrid_volume(crk_plan* plan, crk_stream_t stream, void* ws, int64_t n_s,
+                              const int64_t* box_off_s, const double* x_s, const void* h_s,
+                              double n_h, void* V_out, void* h_out);
+
+/* (k) Normalised kernel deposit (Eqs. windmetal with Anorm, starmetal, AGNE):
+ * each subgrid particle s shares q_s (device real[n_comp][n_s], n_comp <= 64)
+ * among the eligible gas j with r_sj < h_s in proportion to V_j W(r_sj, h_s),
+ * V_j the gas volume of the last crk_moments, normalised by
+ * A_s = 1 / sum_j V_j W(r_sj, h_s).  eligible: optional device uint8[n] in the
+ * gas's caller order (0 excludes a gas particle from both the normalisation
+ * and the deposit, as the paper does for metal-rich or overweight gas).
+ * dq: device real[n_comp][n] in the gas's caller order, ACCUMULATED into
+ * (atomic adds; the caller zeroes it); A_out: optional device real[n_s]
+ * (0 when no eligible gas is in reach: nothing is deposited).
+ * CRK_ESTATE before a crk_moments on this workspace. */
+crk_status crk_subgrid_deposit(crk_plan* plan, crk_stream_t stream, void* ws, int64_t n_s,
+                               const int64_t* box_off_s, const double* x_s, const void* h_s,
+                               int32_t n_comp, const void* q_s, const uint8_t* eligible,
+                               void* A_out, void* dq);
 
 /* ---- Radiative cooling and heating (Sec. 2.3.2, Exact Integration) ----------
  * The source function of du/dt = -Lambda(u; rho)/rho is tabulated as

@@ -76,6 +76,10 @@ _SIGS = {
                                     _VP, _VP]),
     "crk_cool_exact": (C.c_int, [_VP, _VP, C.c_int64, C.POINTER(crk_cool_table), C.c_double, _VP,
                                  _VP, _VP]),
+    "crk_subgrid_volume": (C.c_int, [_VP, _VP, _VP, C.c_int64, _VP, _VP, _VP, C.c_double, _VP,
+                                     _VP]),
+    "crk_subgrid_deposit": (C.c_int, [_VP, _VP, _VP, C.c_int64, _VP, _VP, _VP, C.c_int32, _VP,
+                                      _VP, _VP, _VP]),
     "crk_hdot": (C.c_int, [_VP, _VP, _VP, C.c_double, C.c_double, C.c_double, _VP, _VP, _VP]),
     "crk_kick": (C.c_int, [_VP, _VP, C.c_int64, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "crk_kick_refined": (C.c_int, [_VP, _VP, C.c_int64, C.c_double, C.c_double, _VP, _VP, _VP,
@@ -237,6 +241,18 @@ def crk_drift(plan, stream, n, n_boxes, box_off, box_L, dt, x, v_half, a0=None, 
 def crk_cool_exact(plan, stream, n, table: crk_cool_table, dt, rho, u0, u1) -> int:
     return load().crk_cool_exact(_VP(plan), _VP(stream), int(n), C.byref(table), float(dt),
                                  _VP(rho), _VP(u0), _VP(u1))
+
+
+def crk_subgrid_volume(plan, stream, ws, n_s, box_off_s, x_s, h_s, n_h, V_out, h_out=None):
+    return load().crk_subgrid_volume(_VP(plan), _VP(stream), _VP(ws), int(n_s), _VP(box_off_s),
+                                     _VP(x_s), _VP(h_s), float(n_h), _VP(V_out), _VP(h_out))
+
+
+def crk_subgrid_deposit(plan, stream, ws, n_s, box_off_s, x_s, h_s, n_comp, q_s, eligible, A_out,
+                        dq) -> int:
+    return load().crk_subgrid_deposit(_VP(plan), _VP(stream), _VP(ws), int(n_s), _VP(box_off_s),
+                                      _VP(x_s), _VP(h_s), int(n_comp), _VP(q_s), _VP(eligible),
+                                      _VP(A_out), _VP(dq))
 
 
 SWEEPS = ("b1_volume", "b2_moments", "c1_density", "c2_rates", "adj_c2", "adj_c1", "adj_b2",

@@ -202,6 +202,40 @@ class Solver:
                             _ptr(rho), _ptr(div)), "crk_drift")
         return x
 
+    # -- subgrid particles over the gas of the last build --------------------------
+    def _sub_boxes(self, n_s, box_off_s):
+        if box_off_s is not None:
+            return box_off_s
+        assert self.nb == 1, "pass box_off_s for a multi-box build"
+        return torch.tensor([0, n_s], dtype=torch.int64, device=self.device)
+
+    def subgrid_volume(self, x_s, h_s, n_h=2.25, box_off_s=None, want_h=True):
+        """Scatter volumes of subgrid particles (and n_h V^(1/3))."""
+        n_s = int(h_s.shape[0])
+        bo = self._sub_boxes(n_s, box_off_s)
+        V = torch.empty(n_s, dtype=self.dtype, device=self.device)
+        h = torch.empty(n_s, dtype=self.dtype, device=self.device) if want_h else None
+        L.check(L.crk_subgrid_volume(self.plan, _stream(), self._wsp, n_s, bo.data_ptr(),
+                                     x_s.data_ptr(), h_s.data_ptr(), n_h, V.data_ptr(), _ptr(h)),
+                "crk_subgrid_volume")
+        return V, h
+
+    def subgrid_deposit(self, x_s, h_s, q_s, eligible=None, box_off_s=None, dq=None):
+        """Normalised kernel deposit of q_s (n_comp, n_s) into the gas; returns
+        (dq (n_comp, n), A_s)."""
+        n_s = int(h_s.shape[0])
+        q_s = q_s.reshape(-1, n_s).contiguous()
+        nc = int(q_s.shape[0])
+        bo = self._sub_boxes(n_s, box_off_s)
+        if dq is None:
+            dq = torch.zeros((nc, self.n), dtype=self.dtype, device=self.device)
+        A = torch.empty(n_s, dtype=self.dtype, device=self.device)
+        L.check(L.crk_subgrid_deposit(self.plan, _stream(), self._wsp, n_s, bo.data_ptr(),
+                                      x_s.data_ptr(), h_s.data_ptr(), nc, q_s.data_ptr(),
+                                      _ptr(eligible), A.data_ptr(), dq.data_ptr()),
+                "crk_subgrid_deposit")
+        return dq, A
+
     def cool(self, dt, rho, u, lam, log10_u_min, dlog10_u, out=None):
         """Exact-integration cooling/heating over dt (lam: float64 device tensor
         of Lambda(u_k)/rho^2 at the table nodes)."""
