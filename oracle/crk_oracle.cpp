@@ -764,6 +764,87 @@ int run(int64_t n, const double* x, const double* h, const double* m, const doub
   return nsing > 0 ? ESINGULAR_ : OK;
 }
 
+// Active-set evaluation (App. A.1: passive particles reuse the correction
+// coefficients of their last active step; the power-of-two time bins of Sec. 2
+// decide which particles are active).  flags[i] bit 0: active (density,
+// velocity gradient and rates are evaluated); bit 1: volume and coefficients
+// are recomputed (implied by bit 0).  Every other per-particle field is taken
+// from the given state: V and coefficients for particles without bit 0 or 1,
+// density and velocity gradient for particles without bit 0 (their pressure,
+// sound speed and relaxation flag follow from that density, u and the
+// velocity gradient as for a fresh one).  Stage by stage over the particles
+// that recompute it, so every memoised value a stage reads is complete.
+// Outputs (all optional, caller order, length n): V, coef, rho, gradv for every
+// particle (fresh or state), dvdt, dudt for active particles (0 elsewhere).
+int run_state(int64_t n, const double* x, const double* h, const double* m, const double* v,
+              const double* u, double L, const oracle_params* p, const uint8_t* flags,
+              const double* V_state, const double* coef_state, const double* rho_state,
+              const double* gradv_state, int32_t nthreads, oracle_out* out) {
+  int rc = check_inputs(n, x, h, m, v, u, L);
+  if (rc) return rc;
+  if (!p || !flags || !V_state || !coef_state || !rho_state || !gradv_state) return EINVAL_;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  Box box{n, x, h, L};
+  KDTree tree(&box);
+  Eval<double> E(box, &tree, *p);
+  load_inputs<double>(E, x, h, m, v, u, nullptr, nullptr, nullptr, nullptr);
+  auto active = [flags](int64_t i) { return (flags[i] & 1) != 0; };
+  auto recompute = [flags](int64_t i) { return (flags[i] & 3) != 0; };
+  for (int64_t i = 0; i < n; ++i) {
+    if (!recompute(i)) {
+      E.V[i] = V_state[i];
+      E.doneV[i] = 1;
+      for (int c = 0; c < 16; ++c) E.coef[i][c] = coef_state[c * n + i];
+      E.doneM[i] = 1;
+    }
+    if (!active(i)) {
+      E.rho[i] = rho_state[i];
+      for (int c = 0; c < 9; ++c) E.gradv[i][c] = gradv_state[c * n + i];
+      E.P[i] = (p->gamma - 1.0) * E.rho[i] * E.u[i];
+      E.cs[i] = std::sqrt(p->gamma * (p->gamma - 1.0) * E.u[i]);
+      double div = E.gradv[i][0] + E.gradv[i][4] + E.gradv[i][8];
+      E.flag[i] = (p->relax_dt > 0 && std::exp(std::fabs(div) * p->relax_dt) > 8.0) ? 1 : 0;
+      E.doneR[i] = 1;
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) { E.gather(i); E.unionset(i); if (recompute(i)) E.calcV(i); }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) if (recompute(i)) E.calcMom(i);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) if (active(i)) E.calcRho(i);
+  std::vector<double> dv3(3 * n, 0.0), du(n, 0.0);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    if (!active(i)) continue;
+    double d[3], e;
+    E.calcRates(i, d, e);
+    for (int a = 0; a < 3; ++a) dv3[a * n + i] = d[a];
+    du[i] = e;
+  }
+  int64_t nsing = 0;
+  for (int64_t i = 0; i < n; ++i) nsing += recompute(i) ? E.sing[i] : 0;
+  if (out) {
+    for (int64_t i = 0; i < n; ++i) {
+      if (out->V) out->V[i] = E.V[i];
+      if (out->coef) for (int c = 0; c < 16; ++c) out->coef[c * n + i] = E.coef[i][c];
+      if (out->rho) out->rho[i] = E.rho[i];
+      if (out->gradv) for (int c = 0; c < 9; ++c) out->gradv[c * n + i] = E.gradv[i][c];
+      if (out->P) out->P[i] = E.P[i];
+      if (out->cs) out->cs[i] = E.cs[i];
+      if (out->flag) out->flag[i] = E.flag[i];
+      if (out->dvdt) for (int a = 0; a < 3; ++a) out->dvdt[a * n + i] = dv3[a * n + i];
+      if (out->dudt) out->dudt[i] = du[i];
+    }
+    if (out->nsingular) *out->nsingular = nsing;
+  }
+  return nsing > 0 ? ESINGULAR_ : OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -823,6 +904,16 @@ int oracle_jvp(int64_t n, const double* x, const double* h, const double* m, con
   if (!targets) nt = n;
   return run<Dual>(n, x, h, m, v, u, L, p, tx, th, tv, tu, nt, targets, stages, nthreads,
                    use_tree, out, tout);
+}
+
+// Active-set evaluation; see run_state.
+int oracle_forward_state(int64_t n, const double* x, const double* h, const double* m,
+                         const double* v, const double* u, double L, const oracle_params* p,
+                         const uint8_t* flags, const double* V_state, const double* coef_state,
+                         const double* rho_state, const double* gradv_state, int32_t nthreads,
+                         oracle_out* out) {
+  return run_state(n, x, h, m, v, u, L, p, flags, V_state, coef_state, rho_state, gradv_state,
+                   nthreads, out);
 }
 
 // The kernel itself, for the quadrature and finite-difference pins.

@@ -85,6 +85,10 @@ def _load():
                                        C.POINTER(OracleParams), dp, dp, dp, dp, C.c_int64, dp,
                                        C.c_int32, C.c_int32, C.c_int32, C.POINTER(_Out),
                                        C.POINTER(_Out)]
+            lib.oracle_forward_state.restype = C.c_int
+            lib.oracle_forward_state.argtypes = [C.c_int64, dp, dp, dp, dp, dp, C.c_double,
+                                                 C.POINTER(OracleParams), dp, dp, dp, dp, dp,
+                                                 C.c_int32, C.POINTER(_Out)]
             lib.oracle_neighbors.restype = C.c_int
             lib.oracle_neighbors.argtypes = [C.c_int32, C.c_int32, C.c_int64, dp, dp,
                                              C.c_double, dp, dp, C.c_int64, dp]
@@ -164,6 +168,34 @@ def forward(x, h, m, v=None, u=None, L=1.0, params=None, targets=None,
                             1 if use_tree else 0, C.byref(o))
     if rc not in (0, 6):
         raise ValueError(f"oracle_forward: {STATUS.get(rc, rc)}")
+    arrs["status"] = rc
+    return arrs
+
+
+def forward_state(x, h, m, v, u, L, flags, V_state, coef_state, rho_state, gradv_state,
+                  params=None, nthreads=0):
+    """Active-set evaluation (passive particles reuse stored fields).
+
+    flags (uint8, n): bit 0 active, bit 1 recompute volume and coefficients.
+    State arrays (caller order): V (n,), coef (16, n), rho (n,), gradv (9, n).
+    Returns V, coef, rho, gradv, P, cs, flag for every particle and dvdt,
+    dudt (zero for particles that are not active).
+    """
+    lib = _load()
+    n, x, h, m, v, u = _inputs(x, h, m, v, u)
+    p = params if params is not None else default_params()
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    assert flags.shape == (n,)
+    Vs = _f64(V_state, (n,))
+    cs_ = _f64(coef_state, (16, n))
+    rs = _f64(rho_state, (n,))
+    gs = _f64(gradv_state, (9, n))
+    o, arrs = _alloc(("V", "coef", "rho", "gradv", "P", "cs", "flag", "dvdt", "dudt"), n)
+    rc = lib.oracle_forward_state(n, _ptr(x), _ptr(h), _ptr(m), _ptr(v), _ptr(u), float(L),
+                                  C.byref(p), _ptr(flags), _ptr(Vs), _ptr(cs_), _ptr(rs),
+                                  _ptr(gs), int(nthreads), C.byref(o))
+    if rc not in (0, 6):
+        raise ValueError(f"oracle_forward_state: {STATUS.get(rc, rc)}")
     arrs["status"] = rc
     return arrs
 
