@@ -319,6 +319,7 @@ def run_ours(args, rank, world):
         res["hydro_step"] = hydro_step(args, d, dev, flush)
         res["cooling"] = cooling_leg(args, d, dev, flush)
         res["subgrid"] = subgrid_leg(args, d, dev, flush)
+        res["active_set"] = active_leg(args, d, dev, flush)
     if args.fp64_compare and world == 1 and prec == "mixed":
         res["fp64_gpu"] = fp64_compare(args, d, dev)
         if res["fp64_gpu"]:
@@ -481,6 +482,64 @@ def subgrid_leg(args, d, dev, flush):
     res["n_subgrid"] = n_s
     res["device_status"] = s.poll()
     return res
+
+
+def active_leg(args, d, dev, flush):
+    """Active-set evaluation (App. A.1): one step of a time-bin hierarchy in
+    which a quarter of the particles (whole tree leaves, chosen at random) is
+    active; passive particles reuse their stored coefficients and fields.  The
+    timed call is moments + rates over the active set after one build."""
+    import torch
+    from paper_2511_21921_gb300.solver import Solver
+    n = d["h"].shape[0]
+    prec = args.precision
+    dt_ = torch.float32 if prec == "mixed" else torch.float64
+    t = {"x": torch.tensor(d["x"], dtype=torch.float64, device=dev)}
+    for k in ("h", "m", "u"):
+        t[k] = torch.tensor(d[k], dtype=dt_, device=dev)
+    t["v"] = torch.tensor(d["v"], dtype=dt_, device=dev)
+    s = Solver(n, 1, prec, device=dev)
+    s.cell_build(t["x"], t["h"])
+    V, coef = s.moments(t["m"], want_V=True, want_coef=True)
+    _, _, rho, gv = s.rates(t["v"], t["u"], want_rho=True, want_gradv=True)
+    # leaves (8 consecutive sorted particles) drawn at random: mark one particle
+    # per chosen leaf as transformed and let the library expand it
+    rng = np.random.default_rng(12)
+    flags = torch.zeros(n, dtype=torch.uint8, device=dev)
+    _, leaf = s.leaf_mark(flags, want_leaf=True)
+    lf = leaf.cpu().numpy()
+    chosen = rng.uniform(size=lf.max() + 1) < 0.25
+    fl = np.where(chosen[lf], 1, 0).astype(np.uint8)
+    flags = torch.tensor(fl, device=dev)
+    out = (torch.zeros((3, n), dtype=dt_, device=dev), torch.zeros(n, dtype=dt_, device=dev))
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        k_steps = max(3, min(args.steps, 20))
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k_steps)]
+        for k in range(k_steps):
+            flush.fill_(k & 0xff)
+            evs[k][0].record(stream)
+            fn()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / k_steps
+
+    def full():
+        s.moments(t["m"])
+        s.rates(t["v"], t["u"], out=out)
+
+    def part():
+        s.moments_active(t["m"], flags, V, coef)
+        s.rates_active(t["v"], t["u"], rho, gv, out=out)
+    ms_full = timed(full)
+    ms_part = timed(part)
+    return {"active_fraction": float(fl.mean()), "ms_active_set": round(ms_part, 4),
+            "ms_all_active": round(ms_full, 4), "speedup": round(ms_full / ms_part, 3),
+            "device_status": s.poll()}
 
 
 def fp64_compare(args, d, dev):

@@ -18,6 +18,9 @@
  *                      positions, velocities, internal energies and smoothing
  *                      lengths (no counterpart in the paper; it gives the
  *                      subgrid calibration of Sec. 3 a gradient).
+ *   crk_leaf_mark, crk_moments_active, crk_rates_active
+ *                   -- active-set evaluation: passive particles reuse their
+ *                      stored coefficients and fields (App. A.1).
  *   crk_hdot, crk_kick, crk_kick_refined, crk_drift
  *                   -- the time step around the rates: smoothing-length rate
  *                      and exponential drifts (App. A.3), kick-drift-kick with
@@ -145,6 +148,43 @@ crk_status crk_rates(crk_plan* plan, crk_stream_t stream, void* ws, const void* 
 crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void* v, const void* u,
                        const void* g_dvdt, const void* g_dudt, void* g_x, void* g_v, void* g_u,
                        void* g_h, int32_t recompute);
+
+/* ---- Active-set evaluation (App. A.1; Sec. 2 power-of-two time bins) --------
+ * On a step of a time-bin hierarchy only the active particles update their
+ * forces; passive particles keep the correction coefficients (and volume,
+ * density, velocity gradient) of their last active step.  flags: device
+ * uint8[n], caller order; bit 0 (1) active; bit 1 (2) recompute volume and
+ * coefficients (implied by bit 0); bit 2 (4) transformed (species conversion,
+ * see crk_leaf_mark).  The sweeps run over compacted lists of the flagged
+ * particles; the records of the others are packed from the caller's state
+ * arrays, which persist between steps in the caller's order. */
+
+/* (l) Leaf marking: set bit 1 on every particle sharing a tree leaf (a bucket
+ * of 8 consecutive Morton-sorted particles) with a transformed particle (bit
+ * 2), in place, so that the leaf recomputes its coefficients (App. A.1).
+ * leaf_out: optional device int32[n], the leaf of every particle.  Requires a
+ * built workspace. */
+crk_status crk_leaf_mark(crk_plan* plan, crk_stream_t stream, void* ws, uint8_t* flags,
+                         int32_t* leaf_out);
+
+/* (m) Volume and coefficients of the flagged particles (bit 0 or 1).
+ * V_state: device real[n], coef_state: device real[16][n] (layout of
+ * crk_moments' coef_out), caller order, in/out: written for flagged particles,
+ * read for the others.  Sets up the active list that crk_rates_active uses. */
+crk_status crk_moments_active(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
+                              const uint8_t* flags, void* V_state, void* coef_state);
+
+/* (n) Density, velocity gradient and pair rates of the active particles (bit 0
+ * of the flags given to the last crk_moments_active).  rho_state: device
+ * real[n], gradv_state: device real[9][n], in/out (written for active
+ * particles, read for passive ones, whose pressure, sound speed and relaxation
+ * flag follow from them as for a fresh evaluation).  dvdt real[3][n], dudt
+ * real[n]: written for active particles only.  CRK_ESTATE unless the last
+ * moments call on this workspace was crk_moments_active.  crk_hdot may follow;
+ * crk_adjoint then needs recompute = 1. */
+crk_status crk_rates_active(crk_plan* plan, crk_stream_t stream, void* ws, const void* v,
+                            const void* u, void* rho_state, void* gradv_state, void* dvdt,
+                            void* dudt);
 
 /* ---- Time step around the rates (App. A.3 and A.4) -------------------------
  * A kick-drift-kick step is: crk_kick (half kick with the rates of the last

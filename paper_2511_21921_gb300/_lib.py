@@ -80,6 +80,9 @@ _SIGS = {
                                      _VP]),
     "crk_subgrid_deposit": (C.c_int, [_VP, _VP, _VP, C.c_int64, _VP, _VP, _VP, C.c_int32, _VP,
                                       _VP, _VP, _VP]),
+    "crk_leaf_mark": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "crk_moments_active": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "crk_rates_active": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "crk_hdot": (C.c_int, [_VP, _VP, _VP, C.c_double, C.c_double, C.c_double, _VP, _VP, _VP]),
     "crk_kick": (C.c_int, [_VP, _VP, C.c_int64, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "crk_kick_refined": (C.c_int, [_VP, _VP, C.c_int64, C.c_double, C.c_double, _VP, _VP, _VP,
@@ -253,6 +256,20 @@ def crk_subgrid_deposit(plan, stream, ws, n_s, box_off_s, x_s, h_s, n_comp, q_s,
     return load().crk_subgrid_deposit(_VP(plan), _VP(stream), _VP(ws), int(n_s), _VP(box_off_s),
                                       _VP(x_s), _VP(h_s), int(n_comp), _VP(q_s), _VP(eligible),
                                       _VP(A_out), _VP(dq))
+
+
+def crk_leaf_mark(plan, stream, ws, flags, leaf_out=None) -> int:
+    return load().crk_leaf_mark(_VP(plan), _VP(stream), _VP(ws), _VP(flags), _VP(leaf_out))
+
+
+def crk_moments_active(plan, stream, ws, m, flags, V_state, coef_state) -> int:
+    return load().crk_moments_active(_VP(plan), _VP(stream), _VP(ws), _VP(m), _VP(flags),
+                                     _VP(V_state), _VP(coef_state))
+
+
+def crk_rates_active(plan, stream, ws, v, u, rho_state, gradv_state, dvdt, dudt) -> int:
+    return load().crk_rates_active(_VP(plan), _VP(stream), _VP(ws), _VP(v), _VP(u),
+                                   _VP(rho_state), _VP(gradv_state), _VP(dvdt), _VP(dudt))
 
 
 SWEEPS = ("b1_volume", "b2_moments", "c1_density", "c2_rates", "adj_c2", "adj_c1", "adj_b2",

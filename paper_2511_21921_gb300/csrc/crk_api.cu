@@ -84,6 +84,11 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.adj_acc = take(R * ACC * N);
   L.adj_cbar = take(R * 16 * N);
   L.tune_out = take(R * 12 * N);  // outputs of the autotuner's trial runs
+  L.flg = take(N);
+  L.act_pred = take(2 * 4 * N);
+  L.act_pos = take(2 * 4 * N);
+  L.items_r = take(4 * N);
+  L.items_a = take(4 * N);
   L.total = o;
   return L;
 }
@@ -224,7 +229,7 @@ crk_status crk_cell_build(crk_plan* plan, crk_stream_t stream, void* ws, size_t 
   P.n = n;
   P.nb = n_boxes;
   P.built = true;
-  P.has_moments = P.has_rates = false;
+  P.has_moments = P.has_rates = P.active_moments = false;
   P.ws_built = ws;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
@@ -253,8 +258,70 @@ crk_status crk_moments(crk_plan* plan, crk_stream_t stream, void* ws, const void
   if (s == CRK_OK) {
     P.has_moments = true;
     P.has_rates = false;
+    P.active_moments = false;
   }
   return s;
+}
+
+crk_status crk_moments_active(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
+                              const uint8_t* flags, void* V_state, void* coef_state) {
+  if (!plan) return CRK_EINVAL;
+  Plan& P = plan->impl;
+  crk_status s = check_ws(P, ws);
+  if (s != CRK_OK) return s;
+  if (P.n > 0 && (!m || !flags || !V_state || !coef_state)) return CRK_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  if (P.p.precision == CRK_FP64)
+    s = moments_active_impl<double>(&P, st, w, static_cast<const double*>(m), flags,
+                                    static_cast<double*>(V_state), static_cast<double*>(coef_state));
+  else
+    s = moments_active_impl<float>(&P, st, w, static_cast<const float*>(m), flags,
+                                   static_cast<float*>(V_state), static_cast<float*>(coef_state));
+  if (s == CRK_OK) {
+    P.has_moments = true;
+    P.has_rates = false;
+    P.active_moments = true;
+  }
+  return s;
+}
+
+crk_status crk_rates_active(crk_plan* plan, crk_stream_t stream, void* ws, const void* v,
+                            const void* u, void* rho_state, void* gradv_state, void* dvdt,
+                            void* dudt) {
+  if (!plan) return CRK_EINVAL;
+  Plan& P = plan->impl;
+  crk_status s = check_ws(P, ws);
+  if (s != CRK_OK) return s;
+  if (!P.has_moments || !P.active_moments) return CRK_ESTATE;
+  if (P.n > 0 && (!v || !u || !rho_state || !gradv_state || !dvdt || !dudt)) return CRK_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  if (P.p.precision == CRK_FP64)
+    s = rates_active_impl<double>(&P, st, w, static_cast<const double*>(v),
+                                  static_cast<const double*>(u), static_cast<double*>(rho_state),
+                                  static_cast<double*>(gradv_state), static_cast<double*>(dvdt),
+                                  static_cast<double*>(dudt));
+  else
+    s = rates_active_impl<float>(&P, st, w, static_cast<const float*>(v),
+                                 static_cast<const float*>(u), static_cast<float*>(rho_state),
+                                 static_cast<float*>(gradv_state), static_cast<float*>(dvdt),
+                                 static_cast<float*>(dudt));
+  // the rate records are complete (stored state for passive particles), so
+  // crk_hdot may follow; an adjoint must recompute the full forward state
+  if (s == CRK_OK) P.has_rates = true;
+  return s;
+}
+
+crk_status crk_leaf_mark(crk_plan* plan, crk_stream_t stream, void* ws, uint8_t* flags,
+                         int32_t* leaf_out) {
+  if (!plan) return CRK_EINVAL;
+  Plan& P = plan->impl;
+  crk_status s = check_ws(P, ws);
+  if (s != CRK_OK) return s;
+  if (P.n > 0 && !flags) return CRK_EINVAL;
+  return leaf_mark_impl(&P, reinterpret_cast<cudaStream_t>(stream), static_cast<char*>(ws),
+                        flags, leaf_out);
 }
 
 crk_status crk_rates(crk_plan* plan, crk_stream_t stream, void* ws, const void* v, const void* u,
@@ -286,7 +353,7 @@ crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void
   Plan& P = plan->impl;
   crk_status s = check_ws(P, ws);
   if (s != CRK_OK) return s;
-  if (!P.has_moments || (!recompute && !P.has_rates)) return CRK_ESTATE;
+  if (!P.has_moments || (!recompute && (!P.has_rates || P.active_moments))) return CRK_ESTATE;
   if (P.n > 0 && (!v || !u || !g_dvdt || !g_dudt || !g_x || !g_v || !g_u || !g_h))
     return CRK_EINVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -302,7 +369,10 @@ crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void
                             static_cast<const float*>(g_dvdt), static_cast<const float*>(g_dudt),
                             static_cast<float*>(g_x), static_cast<float*>(g_v),
                             static_cast<float*>(g_u), static_cast<float*>(g_h), recompute);
-  if (s == CRK_OK && recompute) P.has_rates = true;
+  if (s == CRK_OK && recompute) {
+    P.has_rates = true;
+    P.active_moments = false;
+  }
   return s;
 }
 
@@ -394,6 +464,7 @@ crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const voi
   if (s == CRK_OK) {
     P.has_moments = true;
     P.has_rates = true;
+    P.active_moments = false;
   }
   return s;
 }

@@ -37,7 +37,8 @@ struct DevHeader {
   unsigned long long nbr_nodes;    // tree nodes tested by the list build
   unsigned long long nbr_buckets;  // candidate buckets staged by the list build
   int32_t queue[Q_N];
-  int32_t pad1[16];
+  int32_t n_items[2];  // active-set evaluation: recompute-set and active-set sizes
+  int32_t pad1[14];
 };
 
 __device__ __forceinline__ void set_status(DevHeader* h, int code) {
@@ -246,6 +247,8 @@ struct Layout {
   size_t cnt_g = 0, cnt_s = 0, wlen_g = 0, wlen_s = 0, ell = 0;
   size_t rec_b1 = 0, rec_b2 = 0, rec_c1 = 0, rec_c2 = 0, coef = 0, Vs = 0, rhos = 0;
   size_t gvs = 0, Ds = 0;
+  // active-set evaluation: sorted flags, scan scratch, compacted work lists
+  size_t flg = 0, act_pred = 0, act_pos = 0, items_r = 0, items_a = 0;
   // adjoint
   size_t adj_ab = 0, adj_rec1 = 0, adj_rec2 = 0, adj_rec3 = 0, adj_acc = 0, adj_cbar = 0,
          mom = 0, tune_out = 0;

@@ -499,6 +499,236 @@ template crk_status forward_state_impl<float>(Plan*, cudaStream_t, char*, const 
 template crk_status forward_state_impl<double>(Plan*, cudaStream_t, char*, const double*,
                                                const double*);
 
+// ===========================================================================
+// Active-set evaluation (App. A.1: passive particles keep the correction
+// coefficients of their last active step).  flags (caller order) bit 0:
+// active; bit 1: recompute volume and coefficients (implied by bit 0).  The
+// sweeps run over compacted lists of sorted indices; the records of the other
+// particles are packed from the caller's stored state.
+// ===========================================================================
+__global__ void k_active_flags(const uint8_t* __restrict__ flags, const int32_t* __restrict__ perm,
+                               int64_t n, uint8_t* __restrict__ flg, uint32_t* __restrict__ pr,
+                               uint32_t* __restrict__ pa) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint8_t f = flags[perm[s]];
+  const bool a = (f & 1) != 0, r = (f & 3) != 0;
+  flg[s] = (uint8_t)((a ? 1 : 0) | (r ? 2 : 0));
+  pr[s] = r ? 1u : 0u;
+  pa[s] = a ? 1u : 0u;
+}
+
+__global__ void k_compact(const uint32_t* __restrict__ pred, const uint32_t* __restrict__ pos,
+                          int64_t n, int32_t* __restrict__ items) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n && pred[s]) items[pos[s]] = (int32_t)s;
+}
+
+// volume and coefficients of the particles that keep them
+template <class R>
+__global__ void k_pack_state_b(const uint8_t* __restrict__ flg, const int32_t* __restrict__ perm,
+                               int64_t n, const R* __restrict__ xs, const R* __restrict__ V_state,
+                               const R* __restrict__ coef_state, R* __restrict__ rec_b2,
+                               R* __restrict__ Vs, R* __restrict__ coef) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n || (flg[s] & 2)) return;
+  using RC = Rec<R>;
+  const int64_t p = perm[s];
+  R r[RC::B2];
+#pragma unroll
+  for (int k = 0; k < RC::B2; ++k) r[k] = R(0);
+  get_x(xs, n, s, r);
+  const R V = V_state[p];
+  r[RC::B2_V] = V;
+  store_rec<RC::B2>(rec_b2, s, r);
+  Vs[s] = V;
+  R C[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) C[k] = coef_state[k * n + p];
+  store_rec<16>(coef, s, C);
+}
+
+// rate records of the passive particles from their stored density and
+// velocity gradient (pressure, sound speed, viscosity factors and relaxation
+// flag formed as the density sweep forms them)
+template <class R>
+__global__ void k_pack_state_c2(const uint8_t* __restrict__ flg, const int32_t* __restrict__ perm,
+                                int64_t n, const R* __restrict__ xs, const R* __restrict__ hs,
+                                const R* __restrict__ Vs, const R* __restrict__ us,
+                                const R* __restrict__ v, const R* __restrict__ coef,
+                                const R* __restrict__ rho_state, const R* __restrict__ gv_state,
+                                R gm1, R ggm1, R Cl, R Cq, R relax_dt, R* __restrict__ rec_c2,
+                                R* __restrict__ rhos) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n || (flg[s] & 1)) return;
+  using RC = Rec<R>;
+  const int64_t p = perm[s];
+  R r[RC::C2];
+#pragma unroll
+  for (int k = 0; k < RC::C2; ++k) r[k] = R(0);
+  get_x(xs, n, s, r);
+  const R rho = rho_state[p], u = us[s];
+  const R cs = sqrt_(ggm1 * u);
+  R gv[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) gv[k] = gv_state[k * n + p];
+  const R div = gv[0] + gv[4] + gv[8];
+  const bool flag = relax_dt > R(0) && exp_(fabs(div) * relax_dt) > R(8);
+  r[RC::C2_IH] = R(1) / hs[s];
+  r[RC::C2_V] = Vs[s];
+  r[RC::C2_P] = gm1 * rho * u;
+  r[RC::C2_QA] = Cl * rho * cs;
+  r[RC::C2_QB] = Cq * rho;
+  r[RC::C2_FLAG] = flag ? R(1) : R(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r[RC::C2_VEL + k] = v[k * n + p];
+  R C[16];
+  load_rec<16>(coef, s, C);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) r[RC::C2_A + k] = C[k];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) r[RC::C2_GV + k] = gv[k];
+  store_rec<RC::C2>(rec_c2, s, r);
+  rhos[s] = rho;
+}
+
+template <class R>
+crk_status moments_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* m,
+                               const uint8_t* flags, R* V_state, R* coef_state) {
+  const Layout& Ly = plan->ly;
+  const int64_t n = Ly.n;
+  Common c = make_common(plan, ws);
+  cudaMemsetAsync(&c.hdr->queue[Q_B1], 0, 2 * sizeof(int32_t), st);
+  if (n == 0) return CRK_OK;
+  uint8_t* flg = reinterpret_cast<uint8_t*>(ws + Ly.flg);
+  uint32_t* pr = reinterpret_cast<uint32_t*>(ws + Ly.act_pred);
+  uint32_t* pa = pr + n;
+  uint32_t* qr = reinterpret_cast<uint32_t*>(ws + Ly.act_pos);
+  uint32_t* qa = qr + n;
+  int32_t* items_r = reinterpret_cast<int32_t*>(ws + Ly.items_r);
+  int32_t* items_a = reinterpret_cast<int32_t*>(ws + Ly.items_a);
+  const unsigned g = (unsigned)((n + 255) / 256);
+  {
+    Phase ph(plan, st, "active_lists", 5);
+    k_active_flags<<<g, 256, 0, st>>>(flags, c.perm, n, flg, pr, pa);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(c.hdr->n_items);
+    exclusive_scan<uint32_t>(pr, qr, n, ws + Ly.scan_tmp, counts, st);
+    exclusive_scan<uint32_t>(pa, qa, n, ws + Ly.scan_tmp, counts + 1, st);
+    k_compact<<<g, 256, 0, st>>>(pr, qr, n, items_r);
+    k_compact<<<g, 256, 0, st>>>(pa, qa, n, items_a);
+  }
+  R* rec_b1 = reinterpret_cast<R*>(ws + Ly.rec_b1);
+  R* rec_b2 = reinterpret_cast<R*>(ws + Ly.rec_b2);
+  R* ms = reinterpret_cast<R*>(ws + Ly.ms);
+  R* Vs = reinterpret_cast<R*>(ws + Ly.Vs);
+  R* coef = reinterpret_cast<R*>(ws + Ly.coef);
+  const R* xs = reinterpret_cast<const R*>(ws + Ly.xs);
+  const R* hs = reinterpret_cast<const R*>(ws + Ly.hs);
+  {
+    Phase ph(plan, st, "pack_b1", 2);
+    k_pack_b1<R><<<g, 256, 0, st>>>(xs, m, c.perm, n, rec_b1, ms);
+    k_pack_state_b<R><<<g, 256, 0, st>>>(flg, c.perm, n, xs, V_state, coef_state, rec_b2, Vs,
+                                         coef);
+  }
+  Common cr = c;
+  cr.items = items_r;
+  cr.n_items = c.hdr->n_items;
+  typename PassB1<R>::Args a1{cr, rec_b1, hs, rec_b2, Vs, V_state};
+  launch_sweep<PassB1<R>>(plan, st, a1, "b1_volume");
+  typename PassB2<R>::Args a2{cr, rec_b2, hs, coef, reinterpret_cast<R*>(ws + Ly.mom), coef_state};
+  launch_sweep<PassB2<R>>(plan, st, a2, "b2_moments");
+  return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
+}
+
+template <class R>
+crk_status rates_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u,
+                             R* rho_state, R* gv_state, R* dvdt, R* dudt) {
+  const Layout& Ly = plan->ly;
+  const int64_t n = Ly.n;
+  const crk_params& p = plan->p;
+  Common c = make_common(plan, ws);
+  cudaMemsetAsync(&c.hdr->queue[Q_C1], 0, 2 * sizeof(int32_t), st);
+  if (n == 0) return CRK_OK;
+  R* rec_c1 = reinterpret_cast<R*>(ws + Ly.rec_c1);
+  R* rec_c2 = reinterpret_cast<R*>(ws + Ly.rec_c2);
+  R* us = reinterpret_cast<R*>(ws + Ly.us);
+  const unsigned g = (unsigned)((n + 255) / 256);
+  const R gm1 = (R)(p.gamma - 1.0), ggm1 = (R)(p.gamma * (p.gamma - 1.0));
+  {
+    Phase ph(plan, st, "pack_c1", 2);
+    k_pack_c1<R><<<g, 256, 0, st>>>(
+        reinterpret_cast<const R*>(ws + Ly.xs), reinterpret_cast<const R*>(ws + Ly.Vs),
+        reinterpret_cast<const R*>(ws + Ly.ms), v, u, c.perm, n, rec_c1, us);
+    k_pack_state_c2<R><<<g, 256, 0, st>>>(
+        reinterpret_cast<const uint8_t*>(ws + Ly.flg), c.perm, n,
+        reinterpret_cast<const R*>(ws + Ly.xs), reinterpret_cast<const R*>(ws + Ly.hs),
+        reinterpret_cast<const R*>(ws + Ly.Vs), us, v, reinterpret_cast<const R*>(ws + Ly.coef),
+        rho_state, gv_state, gm1, ggm1, (R)p.Cl, (R)p.Cq, (R)p.relax_dt, rec_c2,
+        reinterpret_cast<R*>(ws + Ly.rhos));
+  }
+  Common ca = c;
+  ca.items = reinterpret_cast<const int32_t*>(ws + Ly.items_a);
+  ca.n_items = c.hdr->n_items + 1;
+  typename PassC1<R>::Args a1{ca,
+                              rec_c1,
+                              reinterpret_cast<const R*>(ws + Ly.hs),
+                              reinterpret_cast<const R*>(ws + Ly.coef),
+                              us,
+                              rec_c2,
+                              reinterpret_cast<R*>(ws + Ly.rhos),
+                              reinterpret_cast<R*>(ws + Ly.Ds),
+                              rho_state,
+                              gv_state,
+                              gm1,
+                              ggm1,
+                              (R)p.Cl,
+                              (R)p.Cq,
+                              (R)p.relax_dt};
+  launch_sweep<PassC1<R>>(plan, st, a1, "c1_density");
+  typename PassC2<R>::Args a2{ca, rec_c2, reinterpret_cast<const R*>(ws + Ly.ms), dvdt, dudt,
+                              make_av<R>(p)};
+  launch_sweep<PassC2<R>>(plan, st, a2, "c2_rates");
+  return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
+}
+
+// leaf marking: every particle sharing a tree leaf (bucket of kBucket sorted
+// particles) with a transformed particle (flags bit 2) gets bit 1 (recompute)
+__global__ void k_leaf_mark(const int32_t* __restrict__ perm, int64_t n, uint8_t* flags,
+                            int32_t* __restrict__ leaf_out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = s < n;
+  const int64_t p = live ? perm[s] : 0;
+  const bool tr = live && (flags[p] & 4);
+  const unsigned m = __ballot_sync(kFull, tr);
+  static_assert(32 % kBucket == 0, "buckets tile a warp");
+  const int lane = threadIdx.x & 31;
+  const unsigned grp = ((1u << kBucket) - 1u) << (lane / kBucket * kBucket);
+  if (!live) return;
+  if (m & grp) flags[p] |= 2;
+  if (leaf_out) leaf_out[p] = (int32_t)(s / kBucket);
+}
+
+crk_status leaf_mark_impl(Plan* plan, cudaStream_t st, char* ws, uint8_t* flags,
+                          int32_t* leaf_out) {
+  const int64_t n = plan->ly.n;
+  if (n == 0) return CRK_OK;
+  Phase ph(plan, st, "leaf_mark", 1);
+  // blocks of 256 threads start on bucket boundaries, so a bucket never
+  // straddles two warps
+  k_leaf_mark<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<const int32_t*>(ws + plan->ly.perm), n, flags, leaf_out);
+  return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
+}
+
+template crk_status moments_active_impl<float>(Plan*, cudaStream_t, char*, const float*,
+                                               const uint8_t*, float*, float*);
+template crk_status moments_active_impl<double>(Plan*, cudaStream_t, char*, const double*,
+                                                const uint8_t*, double*, double*);
+template crk_status rates_active_impl<float>(Plan*, cudaStream_t, char*, const float*,
+                                             const float*, float*, float*, float*, float*);
+template crk_status rates_active_impl<double>(Plan*, cudaStream_t, char*, const double*,
+                                              const double*, double*, double*, double*, double*);
+
 template crk_status moments_impl<float>(Plan*, cudaStream_t, char*, const float*, float*, float*);
 template crk_status moments_impl<double>(Plan*, cudaStream_t, char*, const double*, double*,
                                          double*);

@@ -27,6 +27,7 @@ struct Plan {
   bool built = false;
   bool has_moments = false;
   bool has_rates = false;
+  bool active_moments = false;  // the last moments call was an active-set one
   bool sorted_keys_in_key0 = true;
   const void* ws_built = nullptr;
   int64_t n = 0;
@@ -70,6 +71,14 @@ crk_status moments_impl(Plan* plan, cudaStream_t st, char* ws, const R* m, R* V_
 template <class R>
 crk_status rates_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u, R* dvdt,
                       R* dudt, R* rho_out, R* gradv_out);
+template <class R>
+crk_status moments_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* m,
+                               const uint8_t* flags, R* V_state, R* coef_state);
+template <class R>
+crk_status rates_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u,
+                             R* rho_state, R* gv_state, R* dvdt, R* dudt);
+crk_status leaf_mark_impl(Plan* plan, cudaStream_t st, char* ws, uint8_t* flags,
+                          int32_t* leaf_out);
 template <class R>
 crk_status forward_state_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u);
 template <class R>

@@ -19,6 +19,10 @@ struct Common {
   const int32_t* __restrict__ perm;
   int64_t cap_pp;  // list slots per particle: gather part from the front, scatter-only from the back
   int pf;          // prefetch distance in list entries (0 = off)
+  // optional compacted work list (sorted indices; its length on the device):
+  // warps then take 32 listed particles per item instead of 32 consecutive ones
+  const int32_t* items = nullptr;
+  const int32_t* n_items = nullptr;
 };
 
 // Ask L1 for the cache lines of neighbor j's record (base + j*bytes, `bytes`
@@ -123,13 +127,19 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
   const int lane = threadIdx.x & 31;
   int32_t* q = &a.c.hdr->queue[P::QUEUE];
   extern __shared__ float4 ring[];
+  const int64_t nlist = a.c.items ? (int64_t)*a.c.n_items : 0;
+  const int64_t nwork = a.c.items ? (nlist + 31) / 32 : a.c.nw;
   for (;;) {
     int w = 0;
     if (lane == 0) w = atomicAdd(q, 1);
     w = __shfl_sync(kFull, w, 0);
-    if (w >= a.c.nw) break;
-    const int64_t s = (int64_t)w * 32 + lane;
-    const bool live = s < a.c.n;
+    if (w >= nwork) break;
+    int64_t s = (int64_t)w * 32 + lane;
+    bool live = s < a.c.n;
+    if (a.c.items) {
+      live = s < nlist;
+      s = live ? a.c.items[s] : 0;
+    }
     typename P::State st;
     int lg = 0, ls = 0;
     if (live) {
@@ -137,7 +147,8 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
       lg = a.c.cnt_g[s];
       ls = P::GATHER ? 0 : a.c.cnt_s[s];
     }
-    const uint32_t* col = a.c.ell + (int64_t)w * a.c.cap_pp * 32 + lane;
+    // the particle's own list column (warp-interleaved by sorted index)
+    const uint32_t* col = a.c.ell + (s >> 5) * a.c.cap_pp * 32 + (s & 31);
     using Real = typename P::Real;
     if constexpr (STG) {
       // union list (gather part, then scatter-only part) through the ring
@@ -167,7 +178,7 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
       cp_async_wait<0>();
     } else if (P::GATHER) {
       // gather part only: the same row of every lane is one 128-byte line
-      const int wg = a.c.wlen_g[w];
+      const int wg = a.c.items ? __reduce_max_sync(kFull, lg) : a.c.wlen_g[w];
       const int pf = a.c.pf;
       for (int k = 0; k < wg; ++k) {
         if (pf && k + pf < lg)

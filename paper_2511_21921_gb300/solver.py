@@ -158,6 +158,31 @@ class Solver:
                 "crk_adjoint")
         return gx, gv, gu, gh
 
+    # -- active-set evaluation (passive particles reuse their stored fields) -------
+    def leaf_mark(self, flags, want_leaf=False):
+        """Set bit 1 on the leaf-mates of transformed particles (bit 2), in place."""
+        leaf = torch.empty(self.n, dtype=torch.int32, device=self.device) if want_leaf else None
+        L.check(L.crk_leaf_mark(self.plan, _stream(), self._wsp, flags.data_ptr(), _ptr(leaf)),
+                "crk_leaf_mark")
+        return flags, leaf
+
+    def moments_active(self, m, flags, V_state, coef_state):
+        L.check(L.crk_moments_active(self.plan, _stream(), self._wsp, m.data_ptr(),
+                                     flags.data_ptr(), V_state.data_ptr(), coef_state.data_ptr()),
+                "crk_moments_active")
+        return V_state, coef_state
+
+    def rates_active(self, v, u, rho_state, gradv_state, out=None):
+        n = self.n
+        if out is None:
+            out = (torch.zeros((3, n), dtype=self.dtype, device=self.device),
+                   torch.zeros(n, dtype=self.dtype, device=self.device))
+        dvdt, dudt = out
+        L.check(L.crk_rates_active(self.plan, _stream(), self._wsp, v.data_ptr(), u.data_ptr(),
+                                   rho_state.data_ptr(), gradv_state.data_ptr(), dvdt.data_ptr(),
+                                   dudt.data_ptr()), "crk_rates_active")
+        return dvdt, dudt
+
     # -- (e)-(h) time step around the rates --------------------------------------
     def hdot(self, dt_a, lam, n_h, out=None):
         """(hdot, hdot/h, div v) of the last rates evaluation, caller order."""
