@@ -253,7 +253,7 @@ crk_status crk_drift(crk_plan* plan, crk_stream_t stream, int64_t n, int32_t n_b
  * crk_cell_build through its bucket tree.  Subgrid arrays are in the caller's
  * order: box_off_s: device int64[n_boxes+1] (same boxes, same order as the
  * build), x_s: device double[3][n_s] inside their box, h_s: device real[n_s].
- * One thread per subgrid particle; no workspace beyond the built one. */
+ * One warp per subgrid particle; no workspace beyond the built one. */
 
 /* (j) Scatter volume (App. A.2, Eq. Vsg): V_s = 1 / (sum over gas j with
  * r_sj < h_j of W(r_sj, h_j) + W(0, h_s)); optional h_out = n_h V_s^(1/3)
