@@ -79,36 +79,24 @@ __device__ __forceinline__ void rk_gradient_rev(const R* C, const R* x, R W, R g
 }
 
 // Adjoint of rk_coefficients: reduced-moment cotangents mb[29] from the
-// coefficient cotangents Cb[16].  The forward pieces are recomputed with the
-// same precisions as the forward (double inverse of m2, B and A).
+// coefficient cotangents Cb[16], with the inverse of m2, u and A the forward
+// coefficient step stored beside the moments (arithmetic in R throughout).
 template <class R>
 __device__ void rk_coefficients_rev(const R* mom, const R* Cb, R* mb) {
 #pragma unroll
   for (int k = 0; k < 29; ++k) mb[k] = R(0);
-  const double m0 = mom[0];
-  const double m1[3] = {mom[1], mom[2], mom[3]};
-  const double a = mom[4], b = mom[5], c = mom[6], d = mom[7], e = mom[8], f = mom[9];
-  const double c00 = d * f - e * e, c01 = c * e - b * f, c02 = b * e - c * d;
-  const double c11 = a * f - c * c, c12 = b * c - a * e, c22 = a * d - b * b;
-  const double det = a * c00 + b * c01 + c * c02;
-  const double tr = (fabs(a) + fabs(d) + fabs(f)) / 3.0;
-  if (!(fabs(det) > 1e-12 * tr * tr * tr)) return;  // constant fallback: no gradient
-  const double id = 1.0 / det;
-  const double M[3][3] = {{c00 * id, c01 * id, c02 * id},
-                          {c01 * id, c11 * id, c12 * id},
-                          {c02 * id, c12 * id, c22 * id}};
-  double Mm1[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) Mm1[i] = M[i][0] * m1[0] + M[i][1] * m1[1] + M[i][2] * m1[2];
-  const double A = 1.0 / (m0 - (m1[0] * Mm1[0] + m1[1] * Mm1[1] + m1[2] * Mm1[2]));
-  const R Ar = (R)A;
+  if (mom[kMomSing] != R(0)) return;  // constant fallback: no gradient
+  // m2^-1, u = m2^-1 m1 and A as the forward coefficient step formed them
+  const R Ar = mom[kMomA];
   R Mr[3][3], u[3];
+  Mr[0][0] = mom[kMomInv + 0];
+  Mr[0][1] = Mr[1][0] = mom[kMomInv + 1];
+  Mr[0][2] = Mr[2][0] = mom[kMomInv + 2];
+  Mr[1][1] = mom[kMomInv + 3];
+  Mr[1][2] = Mr[2][1] = mom[kMomInv + 4];
+  Mr[2][2] = mom[kMomInv + 5];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    u[i] = (R)Mm1[i];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) Mr[i][k] = (R)M[i][k];
-  }
+  for (int i = 0; i < 3; ++i) u[i] = mom[kMomU + i];
   const R m0r = mom[0];
   const R* m1r = mom + 1;
   const R* S0 = mom + 10;
@@ -178,34 +166,36 @@ __device__ void rk_coefficients_rev(const R* mom, const R* Cb, R* mb) {
     for (int i = 0; i < 3; ++i) mb[13 + s6(i, g)] += d1b[i];
     mb[0] += d1b[g];
   }
-  // A = 1/(m0 - m1.u), B = -u, u = M m1, M = m2^{-1}   (in double)
-  const double a0b = -A * A * (double)Ab;
-  double ubd[3], Mbd[3][3];
+  // A = 1/(m0 - m1.u), B = -u, u = M m1, M = m2^{-1}
+  const R* m1 = mom + 1;
+  const R a0b = -Ar * Ar * Ab;
+  R ubd[3], Mbd[3][3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) ubd[k] = (double)ub[k] - a0b * m1[k] - (double)Cb[1 + k];
-  mb[0] += (R)a0b;
+  for (int k = 0; k < 3; ++k) ubd[k] = ub[k] - a0b * m1[k] - Cb[1 + k];
+  mb[0] += a0b;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    double t = -a0b * Mm1[k];
+    R t = -a0b * u[k];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) t += M[i][k] * ubd[i];
-    mb[1 + k] += (R)t;
+    for (int i = 0; i < 3; ++i) t += Mr[i][k] * ubd[i];
+    mb[1 + k] += t;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) Mbd[i][k] = (double)Mb[i][k] + ubd[i] * m1[k];
-  double T[3][3];
+    for (int k = 0; k < 3; ++k) Mbd[i][k] = Mb[i][k] + ubd[i] * m1[k];
+  R T[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) T[i][k] = M[i][0] * Mbd[0][k] + M[i][1] * Mbd[1][k] + M[i][2] * Mbd[2][k];
+    for (int k = 0; k < 3; ++k)
+      T[i][k] = Mr[i][0] * Mbd[0][k] + Mr[i][1] * Mbd[1][k] + Mr[i][2] * Mbd[2][k];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const double v = -(T[i][0] * M[0][k] + T[i][1] * M[1][k] + T[i][2] * M[2][k]);
-      mb[4 + s6(i, k)] += (R)v;
+      const R v = -(T[i][0] * Mr[0][k] + T[i][1] * Mr[1][k] + T[i][2] * Mr[2][k]);
+      mb[4 + s6(i, k)] += v;
     }
 }
 

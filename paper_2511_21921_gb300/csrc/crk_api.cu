@@ -67,7 +67,7 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.rec_c1 = take(R * C1 * N);
   L.rec_c2 = take(R * C2 * N);
   L.coef = take(R * 16 * N);
-  L.mom = take(R * 32 * N);
+  L.mom = take(R * kMomW * N);
   L.Vs = take(R * N);
   L.rhos = take(R * N);
   L.Ds = take(R * N);

@@ -27,6 +27,12 @@ enum Queue {
   Q_B1 = 0, Q_B2, Q_C1, Q_C2, Q_A_C2, Q_A_C1, Q_A_B2, Q_A_B1, Q_COUNT_, Q_FILL_, Q_N = 16
 };
 
+// Stored per particle by the moment sweep: the 29 reduced moments, then the
+// inverse of m2 (xx, xy, xz, yy, yz, zz), u = m2^-1 m1, A and a singular flag,
+// as the coefficient step formed them (so the adjoint needs no FP64 inverse).
+constexpr int kMomW = 40;
+constexpr int kMomInv = 29, kMomU = 35, kMomA = 38, kMomSing = 39;
+
 struct DevHeader {
   int32_t status;
   int32_t pad0;

@@ -166,10 +166,9 @@ template <class R> struct PassB2 {
     for (int k = 0; k < 6; ++k) { mom[4 + k] = st.m2[k]; mom[13 + k] = st.S2[k]; }
 #pragma unroll
     for (int k = 0; k < 10; ++k) mom[19 + k] = st.S3[k];
-    mom[29] = mom[30] = mom[31] = R(0);
-    store_rec<kMomW>(a.mom, s, mom);
     R C[16];
     bool sing = rk_coefficients<R>(mom, C);
+    store_rec<kMomW>(a.mom, s, mom);
     if (sing) {
       atomicAdd(&a.c.hdr->nsingular, 1ull);
       set_status(a.c.hdr, CRK_ESINGULAR);

@@ -244,7 +244,6 @@ template <class R> struct Acc {
   }
 };
 
-constexpr int kMomW = 32;  // stored reduced moments per particle (29 used)
 
 // sym6 index of (a, b): xx, xy, xz, yy, yz, zz
 __device__ __forceinline__ int s6(int a, int b) {
@@ -264,9 +263,10 @@ __device__ __forceinline__ int s10(int a, int b, int c) {
 
 // Coefficients from the reduced moments.  The 3x3 inverse of m2, B and A
 // are formed in double; the gradient terms in R.  Returns true when m2 is
-// singular (then A = 1 and everything else 0, the uncorrected kernel).
+// singular (then A = 1 and everything else 0, the uncorrected kernel).  The
+// inverse, u and A (rounded to R) and the singular flag go to mom[29..39].
 template <class R>
-__device__ bool rk_coefficients(const R* mom, R* C) {
+__device__ bool rk_coefficients(R* mom, R* C) {
   const double m0 = mom[0];
   const double m1[3] = {mom[1], mom[2], mom[3]};
   const double a = mom[4], b = mom[5], c = mom[6], d = mom[7], e = mom[8], f = mom[9];
@@ -274,10 +274,13 @@ __device__ bool rk_coefficients(const R* mom, R* C) {
   const double c11 = a * f - c * c, c12 = b * c - a * e, c22 = a * d - b * b;
   const double det = a * c00 + b * c01 + c * c02;
   const double tr = (fabs(a) + fabs(d) + fabs(f)) / 3.0;
+#pragma unroll
+  for (int k = kMomInv; k < kMomW; ++k) mom[k] = R(0);
   if (!(fabs(det) > 1e-12 * tr * tr * tr)) {
     C[0] = R(1);
 #pragma unroll
     for (int k = 1; k < 16; ++k) C[k] = R(0);
+    mom[kMomSing] = R(1);
     return true;
   }
   const double id = 1.0 / det;
@@ -300,6 +303,15 @@ __device__ bool rk_coefficients(const R* mom, R* C) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) Mr[i][k] = (R)M[i][k];
   }
+  mom[kMomInv + 0] = Mr[0][0];
+  mom[kMomInv + 1] = Mr[0][1];
+  mom[kMomInv + 2] = Mr[0][2];
+  mom[kMomInv + 3] = Mr[1][1];
+  mom[kMomInv + 4] = Mr[1][2];
+  mom[kMomInv + 5] = Mr[2][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) mom[kMomU + i] = u[i];
+  mom[kMomA] = Ar;
   const R m0r = mom[0];
   const R* m1r = mom + 1;
   const R* S0 = mom + 10;
