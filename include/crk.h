@@ -18,7 +18,7 @@
  *                      positions, velocities, internal energies and smoothing
  *                      lengths (no counterpart in the paper; it gives the
  *                      subgrid calibration of Sec. 3 a gradient).
- *   crk_leaf_mark, crk_moments_active, crk_rates_active
+ *   crk_leaf_mark, crk_time_bins, crk_moments_active, crk_rates_active
  *                   -- active-set evaluation: passive particles reuse their
  *                      stored coefficients and fields (App. A.1).
  *   crk_hdot, crk_kick, crk_kick_refined, crk_drift
@@ -166,6 +166,18 @@ crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void
  * built workspace. */
 crk_status crk_leaf_mark(crk_plan* plan, crk_stream_t stream, void* ws, uint8_t* flags,
                          int32_t* leaf_out);
+
+/* (l') Power-of-two time bins per leaf (Sec. 2; App. A.4): each leaf takes
+ * the level k = the smallest k >= 0 with dt_max / 2^k <= min over its members
+ * of dt (device real[n], caller order, a particle's own time-step limit),
+ * capped at max_level (0..40); level_out (optional device uint8[n], caller
+ * order) receives it.  On sub-step `substep` (0 <= substep < 2^max_level) of
+ * the finest level a leaf is active when substep is a multiple of
+ * 2^(max_level - k); bit 0 of flags (optional device uint8[n], in/out) is set
+ * accordingly and the other bits are kept.  Requires a built workspace. */
+crk_status crk_time_bins(crk_plan* plan, crk_stream_t stream, void* ws, const void* dt,
+                         double dt_max, int32_t max_level, int64_t substep, uint8_t* level_out,
+                         uint8_t* flags);
 
 /* (m) Volume and coefficients of the flagged particles (bit 0 or 1).
  * V_state: device real[n], coef_state: device real[16][n] (layout of

@@ -81,6 +81,7 @@ _SIGS = {
     "crk_subgrid_deposit": (C.c_int, [_VP, _VP, _VP, C.c_int64, _VP, _VP, _VP, C.c_int32, _VP,
                                       _VP, _VP, _VP]),
     "crk_leaf_mark": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "crk_time_bins": (C.c_int, [_VP, _VP, _VP, _VP, C.c_double, C.c_int32, C.c_int64, _VP, _VP]),
     "crk_moments_active": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "crk_rates_active": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "crk_hdot": (C.c_int, [_VP, _VP, _VP, C.c_double, C.c_double, C.c_double, _VP, _VP, _VP]),
@@ -260,6 +261,11 @@ def crk_subgrid_deposit(plan, stream, ws, n_s, box_off_s, x_s, h_s, n_comp, q_s,
 
 def crk_leaf_mark(plan, stream, ws, flags, leaf_out=None) -> int:
     return load().crk_leaf_mark(_VP(plan), _VP(stream), _VP(ws), _VP(flags), _VP(leaf_out))
+
+
+def crk_time_bins(plan, stream, ws, dt, dt_max, max_level, substep, level_out, flags) -> int:
+    return load().crk_time_bins(_VP(plan), _VP(stream), _VP(ws), _VP(dt), float(dt_max),
+                                int(max_level), int(substep), _VP(level_out), _VP(flags))
 
 
 def crk_moments_active(plan, stream, ws, m, flags, V_state, coef_state) -> int:

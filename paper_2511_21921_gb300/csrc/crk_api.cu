@@ -324,6 +324,26 @@ crk_status crk_leaf_mark(crk_plan* plan, crk_stream_t stream, void* ws, uint8_t*
                         flags, leaf_out);
 }
 
+crk_status crk_time_bins(crk_plan* plan, crk_stream_t stream, void* ws, const void* dt,
+                         double dt_max, int32_t max_level, int64_t substep, uint8_t* level_out,
+                         uint8_t* flags) {
+  if (!plan) return CRK_EINVAL;
+  Plan& P = plan->impl;
+  crk_status s = check_ws(P, ws);
+  if (s != CRK_OK) return s;
+  if (!(dt_max > 0.0) || !std::isfinite(dt_max) || max_level < 0 || max_level > 40 ||
+      substep < 0 || substep >= ((int64_t)1 << max_level))
+    return CRK_EINVAL;
+  if (P.n > 0 && (!dt || (!level_out && !flags))) return CRK_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  if (P.p.precision == CRK_FP64)
+    return time_bins_impl<double>(&P, st, w, static_cast<const double*>(dt), dt_max, max_level,
+                                  substep, level_out, flags);
+  return time_bins_impl<float>(&P, st, w, static_cast<const float*>(dt), dt_max, max_level,
+                               substep, level_out, flags);
+}
+
 crk_status crk_rates(crk_plan* plan, crk_stream_t stream, void* ws, const void* v, const void* u,
                      void* dvdt, void* dudt, void* rho_out, void* gradv_out) {
   if (!plan) return CRK_EINVAL;

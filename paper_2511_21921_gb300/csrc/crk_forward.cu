@@ -719,6 +719,54 @@ crk_status leaf_mark_impl(Plan* plan, cudaStream_t st, char* ws, uint8_t* flags,
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }
 
+// Power-of-two time bins per leaf (Sec. 2: hydro interactions on
+// power-of-two bins; App. A.4: leaves grouped into bins).  A leaf's level is
+// the smallest k with dt_max / 2^k <= the smallest time step of its members
+// (capped at max_level); a leaf is active on sub-step t of the finest level
+// when t is a multiple of 2^(max_level - k).
+template <class R>
+__global__ void k_time_bins(const int32_t* __restrict__ perm, int64_t n, const R* __restrict__ dt,
+                            double dt_max, int max_level, int64_t substep, uint8_t* level_out,
+                            uint8_t* flags_out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = s < n;
+  const int64_t p = live ? perm[s] : 0;
+  double d = live ? (double)dt[p] : 1e300;
+  // minimum over the bucket (kBucket consecutive lanes)
+#pragma unroll
+  for (int o = 1; o < kBucket; o <<= 1) d = fmin(d, __shfl_xor_sync(kFull, d, o));
+  if (!live) return;
+  int k = 0;
+  double t = dt_max;
+  while (k < max_level && t > d) {
+    t *= 0.5;
+    ++k;
+  }
+  const int64_t period = (int64_t)1 << (max_level - k);
+  if (level_out) level_out[p] = (uint8_t)k;
+  if (flags_out) {
+    const bool act = (substep % period) == 0;
+    flags_out[p] = (uint8_t)((flags_out[p] & ~1u) | (act ? 1u : 0u));
+  }
+}
+
+template <class R>
+crk_status time_bins_impl(Plan* plan, cudaStream_t st, char* ws, const R* dt, double dt_max,
+                          int max_level, int64_t substep, uint8_t* level_out, uint8_t* flags_out) {
+  const int64_t n = plan->ly.n;
+  if (n == 0) return CRK_OK;
+  Phase ph(plan, st, "time_bins", 1);
+  // 256-thread blocks start on bucket boundaries: a bucket never straddles warps
+  k_time_bins<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<const int32_t*>(ws + plan->ly.perm), n, dt, dt_max, max_level, substep,
+      level_out, flags_out);
+  return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
+}
+template crk_status time_bins_impl<float>(Plan*, cudaStream_t, char*, const float*, double, int,
+                                          int64_t, uint8_t*, uint8_t*);
+template crk_status time_bins_impl<double>(Plan*, cudaStream_t, char*, const double*, double, int,
+                                           int64_t, uint8_t*, uint8_t*);
+
 template crk_status moments_active_impl<float>(Plan*, cudaStream_t, char*, const float*,
                                                const uint8_t*, float*, float*);
 template crk_status moments_active_impl<double>(Plan*, cudaStream_t, char*, const double*,

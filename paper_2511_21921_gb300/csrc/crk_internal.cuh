@@ -77,6 +77,9 @@ crk_status moments_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* m
 template <class R>
 crk_status rates_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u,
                              R* rho_state, R* gv_state, R* dvdt, R* dudt);
+template <class R>
+crk_status time_bins_impl(Plan* plan, cudaStream_t st, char* ws, const R* dt, double dt_max,
+                          int max_level, int64_t substep, uint8_t* level_out, uint8_t* flags_out);
 crk_status leaf_mark_impl(Plan* plan, cudaStream_t st, char* ws, uint8_t* flags,
                           int32_t* leaf_out);
 template <class R>

@@ -166,6 +166,15 @@ class Solver:
                 "crk_leaf_mark")
         return flags, leaf
 
+    def time_bins(self, dt, dt_max, max_level, substep, flags=None):
+        """Per-leaf power-of-two levels and the active bit for one sub-step."""
+        level = torch.empty(self.n, dtype=torch.uint8, device=self.device)
+        if flags is None:
+            flags = torch.zeros(self.n, dtype=torch.uint8, device=self.device)
+        L.check(L.crk_time_bins(self.plan, _stream(), self._wsp, dt.data_ptr(), dt_max, max_level,
+                                substep, level.data_ptr(), flags.data_ptr()), "crk_time_bins")
+        return level, flags
+
     def moments_active(self, m, flags, V_state, coef_state):
         L.check(L.crk_moments_active(self.plan, _stream(), self._wsp, m.data_ptr(),
                                      flags.data_ptr(), V_state.data_ptr(), coef_state.data_ptr()),

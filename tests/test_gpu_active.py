@@ -131,3 +131,40 @@ def test_leaf_mark_and_call_order():
     rc = L.crk_adjoint(s.plan, 0, s._wsp, t["v"].data_ptr(), t["u"].data_ptr(), g.data_ptr(),
                        z.data_ptr(), g.data_ptr(), g.data_ptr(), z.data_ptr(), z.data_ptr(), 0)
     assert rc == L.CRK_ESTATE
+
+
+def test_power_of_two_time_bins_per_leaf():
+    """Leaf levels (Sec. 2 power-of-two bins, App. A.4 leaves): one level per
+    leaf, the coarsest bin dt_max/2^k not above the leaf's smallest time step,
+    and activity on sub-step t iff t is a multiple of 2^(max_level - k)."""
+    d = synth.load("lognormal32")
+    n = d["h"].shape[0]
+    t = to_dev(d, "mixed")
+    s = Solver(n, 1, "mixed")
+    s.cell_build(t["x"], t["h"])
+    rng = np.random.default_rng(3)
+    dt = (10 ** rng.uniform(-3.5, 0.2, n)).astype(np.float32)
+    max_level, dt_max = 10, 1.0
+    flags0 = rng.choice(np.array([0, 2, 4, 6], np.uint8), size=n)
+    _, leaf = s.leaf_mark(torch.zeros(n, dtype=torch.uint8, device="cuda"), want_leaf=True)
+    leaf = leaf.cpu().numpy()
+    for sub in (0, 1, 2, 3, 8, 512, 1023):
+        flags = torch.tensor(flags0, device="cuda")
+        level, flags = s.time_bins(torch.tensor(dt, device="cuda"), dt_max, max_level, sub, flags)
+        lv = level.cpu().numpy().astype(int)
+        fl = flags.cpu().numpy()
+        nl = leaf.max() + 1
+        lmin = np.full(nl, np.inf)
+        np.minimum.at(lmin, leaf, dt.astype(np.float64))
+        lo = np.full(nl, 99)
+        hi = np.full(nl, -1)
+        np.minimum.at(lo, leaf, lv)
+        np.maximum.at(hi, leaf, lv)
+        assert np.array_equal(lo, hi)  # one level per leaf
+        k = lv
+        ok = (dt_max / 2.0 ** k <= lmin[leaf]) | (k == max_level)
+        tight = (k == 0) | (dt_max / 2.0 ** (k - 1) > lmin[leaf])
+        assert np.all(ok) and np.all(tight)
+        act = (sub % (2 ** (max_level - k))) == 0
+        assert np.array_equal((fl & 1) != 0, act)
+        assert np.array_equal(fl & ~np.uint8(1), flags0 & ~np.uint8(1))
