@@ -295,8 +295,12 @@ struct Eval {
   // neighbor lists (memoised)
   std::vector<std::vector<int64_t>> G, U;
   std::vector<char> hasG, hasU;
+  // species: 0 gas, 1 wind (Sec. 2.5.1: winds enter the gas density, Eq. rhow,
+  // but no hydrodynamic force); empty = all gas
+  std::vector<uint8_t> sp;
+  bool wind(int64_t j) const { return !sp.empty() && sp[j] != 0; }
   // per-particle stage results (memoised)
-  std::vector<T> V;
+  std::vector<T> V, Vgw;
   std::vector<std::array<T, 40>> mom;
   std::vector<std::array<T, 16>> coef;
   std::vector<T> rho, P, cs;
@@ -309,7 +313,7 @@ struct Eval {
     for (int a = 0; a < 3; ++a) { x[a].resize(n); v[a].resize(n); }
     h.resize(n); m.resize(n); u.resize(n);
     G.resize(n); U.resize(n); hasG.assign(n, 0); hasU.assign(n, 0);
-    V.resize(n); mom.resize(n); coef.resize(n);
+    V.resize(n); Vgw.resize(n); mom.resize(n); coef.resize(n);
     rho.resize(n); P.resize(n); cs.resize(n); gradv.resize(n); flag.assign(n, 0);
     doneV.assign(n, 0); doneM.assign(n, 0); doneR.assign(n, 0); sing.assign(n, 0);
   }
@@ -347,17 +351,23 @@ struct Eval {
   }
   static T dot3(const T a[3], const T b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
-  // ---- volume, Eq. Vg:  V_i = m_i / sum_{j in G(i)} m_j W(r_ij, h_i)
+  // ---- volume, Eq. Vg:  V_i = m_i / sum_{j in G(i), gas} m_j W(r_ij, h_i), and
+  // the volume over gas and wind neighbors, V_{g+w} (App. A.2), that the
+  // density uses.  A wind particle's V is its V_{g+w} (it takes no part in the
+  // gas-only sums).
   void calcV(int64_t i) {
     const auto& nb = gather(i);
-    T s(0.0);
+    T s(0.0), sa(0.0);
     for (int64_t j : nb) {
       T xij[3];
       sep(i, j, xij);
       T r = (j == i) ? T(0.0) : sqrt(dot3(xij, xij));
-      s += m[j] * kernel_W(r, h[i]);
+      T w = m[j] * kernel_W(r, h[i]);
+      if (!wind(j)) s += w;
+      sa += w;
     }
-    V[i] = m[i] / s;
+    Vgw[i] = m[i] / sa;
+    V[i] = wind(i) ? Vgw[i] : m[i] / s;
     doneV[i] = 1;
   }
   void ensureV(int64_t i) { if (!doneV[i]) calcV(i); }
@@ -375,6 +385,7 @@ struct Eval {
     T* m0 = &M[0]; T* m1 = &M[1]; T* m2 = &M[4];
     T* dm0 = &M[10]; T* dm1 = &M[13]; T* dm2 = &M[22];
     for (int64_t j : nb) {
+      if (wind(j)) continue;  // the corrections reproduce over the gas
       ensureV(j);
       T xij[3];
       sep(i, j, xij);
@@ -513,8 +524,11 @@ struct Eval {
       sep(i, j, xij);
       T WR, Gr[3];
       corrected(i, xij, j == i, true, WR, Gr);
-      num += m[j] * V[j] * WR;
-      den += V[j] * V[j] * WR;
+      // density over gas and wind (Eq. rhow) with V_{g+w}; velocity gradient
+      // over the gas (Eq. gradv)
+      num += m[j] * Vgw[j] * WR;
+      den += Vgw[j] * Vgw[j] * WR;
+      if (wind(j)) continue;
       for (int a = 0; a < 3; ++a) {
         T dv = v[a][i] - v[a][j];
         for (int b = 0; b < 3; ++b) gv[a * 3 + b] -= V[j] * dv * Gr[b];
@@ -541,6 +555,7 @@ struct Eval {
     T acc[3] = {T(0.0), T(0.0), T(0.0)};
     T eacc(0.0);
     for (int64_t j : nb) {
+      if (wind(i) || wind(j)) continue;  // winds feel and exert no hydro force
       ensureRho(j);
       T xij[3], xji[3];
       sep(i, j, xij);
@@ -676,7 +691,8 @@ template <class T>
 int run(int64_t n, const double* x, const double* h, const double* m, const double* v,
         const double* u, double L, const oracle_params* p, const double* tx, const double* th,
         const double* tv, const double* tu, int64_t nt, const int64_t* targets, int32_t stages,
-        int32_t nthreads, int32_t use_tree, oracle_out* out, oracle_out* tout) {
+        int32_t nthreads, int32_t use_tree, oracle_out* out, oracle_out* tout,
+        const uint8_t* species = nullptr, double* Vgw_out = nullptr) {
   int rc = check_inputs(n, x, h, m, v, u, L);
   if (rc) return rc;
   if (nt < 0 || stages < 1 || stages > 4 || !p) return EINVAL_;
@@ -691,6 +707,7 @@ int run(int64_t n, const double* x, const double* h, const double* m, const doub
   KDTree* tree = use_tree ? new KDTree(&box) : nullptr;
   Eval<T> E(box, tree, *p);
   load_inputs<T>(E, x, h, m, v, u, tx, th, tv, tu);
+  if (species) E.sp.assign(species, species + n);
   const bool all = (targets == nullptr);
   if (all) {
     // Whole-box evaluation: run each stage for every particle, in stage order,
@@ -737,6 +754,7 @@ int run(int64_t n, const double* x, const double* h, const double* m, const doub
     for (int64_t k = 0; k < nt; ++k) {
       int64_t i = all ? k : targets[k];
       if (o->V) o->V[k] = pick(E.V[i]);
+      if (side == 0 && Vgw_out) Vgw_out[k] = val(E.Vgw[i]);
       if (stages >= 2) {
         if (o->coef) for (int c = 0; c < 16; ++c) o->coef[c * nt + k] = pick(E.coef[i][c]);
         if (o->mom) for (int c = 0; c < 40; ++c) o->mom[c * nt + k] = pick(E.mom[i][c]);
@@ -797,6 +815,7 @@ int run_state(int64_t n, const double* x, const double* h, const double* m, cons
   for (int64_t i = 0; i < n; ++i) {
     if (!recompute(i)) {
       E.V[i] = V_state[i];
+      E.Vgw[i] = V_state[i];  // all gas in the active-set evaluation
       E.doneV[i] = 1;
       for (int c = 0; c < 16; ++c) E.coef[i][c] = coef_state[c * n + i];
       E.doneM[i] = 1;
@@ -890,6 +909,19 @@ int oracle_forward(int64_t n, const double* x, const double* h, const double* m,
   if (!targets) nt = n;
   return run<double>(n, x, h, m, v, u, L, p, nullptr, nullptr, nullptr, nullptr, nt, targets,
                      stages, nthreads, use_tree, out, nullptr);
+}
+
+// Forward evaluation with species (0 gas, 1 wind): winds enter the density
+// (Eq. rhow, with the volume over gas and wind, returned in Vgw_out when
+// given) and no other sum.  Otherwise as oracle_forward.
+int oracle_forward_species(int64_t n, const double* x, const double* h, const double* m,
+                           const double* v, const double* u, double L, const oracle_params* p,
+                           const uint8_t* species, int64_t nt, const int64_t* targets,
+                           int32_t stages, int32_t nthreads, int32_t use_tree, oracle_out* out,
+                           double* Vgw_out) {
+  if (!targets) nt = n;
+  return run<double>(n, x, h, m, v, u, L, p, nullptr, nullptr, nullptr, nullptr, nt, targets,
+                     stages, nthreads, use_tree, out, nullptr, species, Vgw_out);
 }
 
 // Jacobian-vector product by forward-mode dual numbers: the tangent of every

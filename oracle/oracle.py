@@ -85,6 +85,11 @@ def _load():
                                        C.POINTER(OracleParams), dp, dp, dp, dp, C.c_int64, dp,
                                        C.c_int32, C.c_int32, C.c_int32, C.POINTER(_Out),
                                        C.POINTER(_Out)]
+            lib.oracle_forward_species.restype = C.c_int
+            lib.oracle_forward_species.argtypes = [C.c_int64, dp, dp, dp, dp, dp, C.c_double,
+                                                   C.POINTER(OracleParams), dp, C.c_int64, dp,
+                                                   C.c_int32, C.c_int32, C.c_int32,
+                                                   C.POINTER(_Out), dp]
             lib.oracle_forward_state.restype = C.c_int
             lib.oracle_forward_state.argtypes = [C.c_int64, dp, dp, dp, dp, dp, C.c_double,
                                                  C.POINTER(OracleParams), dp, dp, dp, dp, dp,
@@ -168,6 +173,35 @@ def forward(x, h, m, v=None, u=None, L=1.0, params=None, targets=None,
                             1 if use_tree else 0, C.byref(o))
     if rc not in (0, 6):
         raise ValueError(f"oracle_forward: {STATUS.get(rc, rc)}")
+    arrs["status"] = rc
+    return arrs
+
+
+def forward_species(x, h, m, v, u, L, species, params=None, targets=None,
+                    want=("V", "coef", "rho", "gradv", "P", "cs", "flag", "dvdt", "dudt"),
+                    nthreads=0):
+    """Evaluation with species (uint8, 0 gas, 1 wind; Sec. 2.5.1, App. A.2):
+    winds enter the density with the volume over gas and wind (returned as
+    "Vgw") and take part in no other sum; their rates are zero."""
+    lib = _load()
+    n, x, h, m, v, u = _inputs(x, h, m, v, u)
+    p = params if params is not None else default_params()
+    sp = np.ascontiguousarray(species, dtype=np.uint8)
+    assert sp.shape == (n,)
+    stages = max(_STAGE_OF[k] for k in want)
+    if targets is not None:
+        targets = np.ascontiguousarray(targets, dtype=np.int64)
+        nt = targets.shape[0]
+    else:
+        nt = n
+    o, arrs = _alloc(want, nt)
+    vgw = np.zeros(nt)
+    rc = lib.oracle_forward_species(n, _ptr(x), _ptr(h), _ptr(m), _ptr(v), _ptr(u), float(L),
+                                    C.byref(p), _ptr(sp), nt, _ptr(targets), stages,
+                                    int(nthreads), 1, C.byref(o), _ptr(vgw))
+    if rc not in (0, 6):
+        raise ValueError(f"oracle_forward_species: {STATUS.get(rc, rc)}")
+    arrs["Vgw"] = vgw
     arrs["status"] = rc
     return arrs
 
