@@ -18,6 +18,8 @@
  *                      positions, velocities, internal energies and smoothing
  *                      lengths (no counterpart in the paper; it gives the
  *                      subgrid calibration of Sec. 3 a gradient).
+ *   crk_set_species, crk_volume_gw
+ *                   -- wind particles in the gas density (Sec. 2.5.1).
  *   crk_leaf_mark, crk_time_bins, crk_moments_active, crk_rates_active
  *                   -- active-set evaluation: passive particles reuse their
  *                      stored coefficients and fields (App. A.1).
@@ -148,6 +150,27 @@ crk_status crk_rates(crk_plan* plan, crk_stream_t stream, void* ws, const void* 
 crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void* v, const void* u,
                        const void* g_dvdt, const void* g_dudt, void* g_x, void* g_v, void* g_u,
                        void* g_h, int32_t recompute);
+
+/* ---- Gas and wind (Sec. 2.5.1, Eq. rhow; App. A.2) -----------------------------
+ * Wind particles live in the same boxes, tree and lists as the gas but take
+ * part in the density only: the gas density sums over gas and wind neighbors
+ * with the volume over gas and wind, V_{g+w}; volume, coefficients, velocity
+ * gradient and pair rates stay gas-only; winds get zero rates and, as the
+ * subgrid particles they are, are skipped by crk_subgrid_*.  A wind particle's
+ * coefficients are reproduced over its gas neighbors (a wind far from gas falls
+ * back to the uncorrected kernel without setting CRK_ESINGULAR) and its V is
+ * its V_{g+w}. */
+
+/* (o) Species of the particles of the last crk_cell_build: device uint8[n],
+ * caller order, 0 gas, nonzero wind; NULL returns to all gas.  Call after
+ * every crk_cell_build (a build clears it) and before crk_moments.  With winds
+ * present crk_adjoint and the active-set calls return CRK_ESTATE. */
+crk_status crk_set_species(crk_plan* plan, crk_stream_t stream, void* ws,
+                           const uint8_t* species);
+
+/* (p) The volume over gas and wind of the last crk_moments, device real[n],
+ * caller order (equal to crk_moments' V_out when there are no winds). */
+crk_status crk_volume_gw(crk_plan* plan, crk_stream_t stream, void* ws, void* Vgw_out);
 
 /* ---- Active-set evaluation (App. A.1; Sec. 2 power-of-two time bins) --------
  * On a step of a time-bin hierarchy only the active particles update their

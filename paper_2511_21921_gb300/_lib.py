@@ -80,6 +80,8 @@ _SIGS = {
                                      _VP]),
     "crk_subgrid_deposit": (C.c_int, [_VP, _VP, _VP, C.c_int64, _VP, _VP, _VP, C.c_int32, _VP,
                                       _VP, _VP, _VP]),
+    "crk_set_species": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "crk_volume_gw": (C.c_int, [_VP, _VP, _VP, _VP]),
     "crk_leaf_mark": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "crk_time_bins": (C.c_int, [_VP, _VP, _VP, _VP, C.c_double, C.c_int32, C.c_int64, _VP, _VP]),
     "crk_moments_active": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -261,6 +263,14 @@ def crk_subgrid_deposit(plan, stream, ws, n_s, box_off_s, x_s, h_s, n_comp, q_s,
 
 def crk_leaf_mark(plan, stream, ws, flags, leaf_out=None) -> int:
     return load().crk_leaf_mark(_VP(plan), _VP(stream), _VP(ws), _VP(flags), _VP(leaf_out))
+
+
+def crk_set_species(plan, stream, ws, species) -> int:
+    return load().crk_set_species(_VP(plan), _VP(stream), _VP(ws), _VP(species))
+
+
+def crk_volume_gw(plan, stream, ws, Vgw_out) -> int:
+    return load().crk_volume_gw(_VP(plan), _VP(stream), _VP(ws), _VP(Vgw_out))
 
 
 def crk_time_bins(plan, stream, ws, dt, dt_max, max_level, substep, level_out, flags) -> int:

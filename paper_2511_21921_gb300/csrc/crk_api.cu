@@ -85,6 +85,8 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.adj_cbar = take(R * 16 * N);
   L.tune_out = take(R * 12 * N);  // outputs of the autotuner's trial runs
   L.flg = take(N);
+  L.spec = take(N);
+  L.Vgws = take(R * N);
   L.act_pred = take(2 * 4 * N);
   L.act_pos = take(2 * 4 * N);
   L.items_r = take(4 * N);
@@ -229,7 +231,7 @@ crk_status crk_cell_build(crk_plan* plan, crk_stream_t stream, void* ws, size_t 
   P.n = n;
   P.nb = n_boxes;
   P.built = true;
-  P.has_moments = P.has_rates = P.active_moments = false;
+  P.has_moments = P.has_rates = P.active_moments = P.species = false;
   P.ws_built = ws;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
@@ -270,6 +272,7 @@ crk_status crk_moments_active(crk_plan* plan, crk_stream_t stream, void* ws, con
   crk_status s = check_ws(P, ws);
   if (s != CRK_OK) return s;
   if (P.n > 0 && (!m || !flags || !V_state || !coef_state)) return CRK_EINVAL;
+  if (P.species) return CRK_ESTATE;  // active sets cover gas-only configurations
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
   if (P.p.precision == CRK_FP64)
@@ -324,6 +327,35 @@ crk_status crk_leaf_mark(crk_plan* plan, crk_stream_t stream, void* ws, uint8_t*
                         flags, leaf_out);
 }
 
+crk_status crk_set_species(crk_plan* plan, crk_stream_t stream, void* ws,
+                           const uint8_t* species) {
+  if (!plan) return CRK_EINVAL;
+  Plan& P = plan->impl;
+  crk_status s = check_ws(P, ws);
+  if (s != CRK_OK) return s;
+  P.has_moments = P.has_rates = P.active_moments = false;
+  if (!species) {
+    P.species = false;
+    return CRK_OK;
+  }
+  s = species_impl(&P, reinterpret_cast<cudaStream_t>(stream), static_cast<char*>(ws), species);
+  if (s == CRK_OK) P.species = true;
+  return s;
+}
+
+crk_status crk_volume_gw(crk_plan* plan, crk_stream_t stream, void* ws, void* Vgw_out) {
+  if (!plan) return CRK_EINVAL;
+  Plan& P = plan->impl;
+  crk_status s = check_ws(P, ws);
+  if (s != CRK_OK) return s;
+  if (!P.has_moments) return CRK_ESTATE;
+  if (P.n > 0 && !Vgw_out) return CRK_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (P.p.precision == CRK_FP64)
+    return volume_gw_impl<double>(&P, st, static_cast<char*>(ws), static_cast<double*>(Vgw_out));
+  return volume_gw_impl<float>(&P, st, static_cast<char*>(ws), static_cast<float*>(Vgw_out));
+}
+
 crk_status crk_time_bins(crk_plan* plan, crk_stream_t stream, void* ws, const void* dt,
                          double dt_max, int32_t max_level, int64_t substep, uint8_t* level_out,
                          uint8_t* flags) {
@@ -374,6 +406,7 @@ crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void
   crk_status s = check_ws(P, ws);
   if (s != CRK_OK) return s;
   if (!P.has_moments || (!recompute && (!P.has_rates || P.active_moments))) return CRK_ESTATE;
+  if (P.species) return CRK_ESTATE;  // the adjoint covers gas-only configurations
   if (P.n > 0 && (!v || !u || !g_dvdt || !g_dudt || !g_x || !g_v || !g_u || !g_h))
     return CRK_EINVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -77,12 +77,14 @@ template <class R> struct Rec {
   static constexpr int XW = Prec<R>::XW;
   static constexpr int VEC = Prec<R>::VEC;
   // b1 (volume): x, m
-  static constexpr int B1_M = XW, B1 = round_up(XW + 1, VEC);
+  static constexpr int B1_M = XW, B1_SP = XW + 1, B1 = round_up(XW + 2, VEC);
   // b2 (moments): x, V
-  static constexpr int B2_V = XW, B2 = round_up(XW + 1, VEC);
+  static constexpr int B2_V = XW, B2_SP = XW + 1, B2 = round_up(XW + 2, VEC);
   // c1 (density, grad v): x, V, m, v[3]
   // (48 bytes in float: three 128-bit loads beat two 256-bit loads of a padded 64)
-  static constexpr int C1_V = XW, C1_M = XW + 1, C1_VEL = XW + 2, C1 = round_up(XW + 5, VEC / 2);
+  // C1_VGW: the volume over gas and wind, negative for a wind particle
+  static constexpr int C1_V = XW, C1_M = XW + 1, C1_VEL = XW + 2, C1_VGW = XW + 5,
+                       C1 = round_up(XW + 6, VEC / 2);
   // c2 (rates): x, ih, V, P, qa, qb, flag, v[3], A, B[3], dA[3], dB[9], gv[9]
   static constexpr int C2_IH = XW, C2_V = XW + 1, C2_P = XW + 2, C2_QA = XW + 3,
                        C2_QB = XW + 4, C2_FLAG = XW + 5, C2_VEL = XW + 6, C2_A = XW + 9,
@@ -255,6 +257,8 @@ struct Layout {
   size_t gvs = 0, Ds = 0;
   // active-set evaluation: sorted flags, scan scratch, compacted work lists
   size_t flg = 0, act_pred = 0, act_pos = 0, items_r = 0, items_a = 0;
+  // species (0 gas, 1 wind) in sorted order, volume over gas and wind
+  size_t spec = 0, Vgws = 0;
   // adjoint
   size_t adj_ab = 0, adj_rec1 = 0, adj_rec2 = 0, adj_rec3 = 0, adj_acc = 0, adj_cbar = 0,
          mom = 0, tune_out = 0;

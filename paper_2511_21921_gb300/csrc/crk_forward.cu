@@ -13,7 +13,7 @@ namespace crk {
 template <class R>
 __global__ void k_pack_b1(const R* __restrict__ xs, const R* __restrict__ m,
                           const int32_t* __restrict__ perm, int64_t n, R* __restrict__ rec,
-                          R* __restrict__ ms) {
+                          R* __restrict__ ms, const uint8_t* __restrict__ spec) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   using RC = Rec<R>;
@@ -23,12 +23,15 @@ __global__ void k_pack_b1(const R* __restrict__ xs, const R* __restrict__ m,
   get_x(xs, n, s, r);
   R mm = m[perm[s]];
   r[RC::B1_M] = mm;
+  r[RC::B1_SP] = (spec && spec[s]) ? R(1) : R(0);
   ms[s] = mm;
   store_rec<RC::B1>(rec, s, r);
 }
 
 // ===========================================================================
-// b1: volume  V_i = m_i / sum_{j in G(i)} m_j W(r_ij, h_i)   (Eq. Vg)
+// b1: volume  V_i = m_i / sum_{j in G(i), gas} m_j W(r_ij, h_i)   (Eq. Vg),
+// and the volume over gas and wind neighbors that the density uses (App.
+// A.2); a wind particle's V is that one.  Without winds the two coincide.
 // ===========================================================================
 template <class R> struct PassB1 {
   static constexpr bool GATHER = true;
@@ -48,7 +51,8 @@ template <class R> struct PassB1 {
   };
   struct State {
     R x[RC::XW];
-    R ih, L, halfL, m, sum;
+    R ih, L, halfL, m, sum, suma;
+    bool wind;
   };
   __device__ static void begin(const Args& a, int64_t s, State& st) {
     R r[RC::B1];
@@ -56,6 +60,8 @@ template <class R> struct PassB1 {
 #pragma unroll
     for (int k = 0; k < RC::XW; ++k) st.x[k] = r[k];
     st.m = r[RC::B1_M];
+    st.wind = r[RC::B1_SP] != R(0);
+    st.suma = R(0);
     st.ih = R(1) / a.hs[s];
     double L = a.c.box_L[a.c.boxid[s]];
     st.L = (R)L;
@@ -70,19 +76,24 @@ template <class R> struct PassB1 {
     separation(st.x, r, st.L, st.halfL, d);
     R W, g;
     wendland(radius(dot3(d, d)), st.ih, W, g);
-    st.sum += r[RC::B1_M] * W;
+    const R w = r[RC::B1_M] * W;
+    st.suma += w;
+    if (r[RC::B1_SP] == R(0)) st.sum += w;
   }
   __device__ static void end(const Args& a, int64_t s, State& st) {
-    R sum = st.sum + st.m * wendland0(st.ih);
-    R V = st.m / sum;
+    const R self = st.m * wendland0(st.ih);
+    const R Vgw = st.m / (st.suma + self);
+    const R V = st.wind ? Vgw : st.m / (st.sum + self);
     R r[RC::B2];
 #pragma unroll
     for (int k = 0; k < RC::B2; ++k) r[k] = R(0);
 #pragma unroll
     for (int k = 0; k < RC::XW; ++k) r[k] = st.x[k];
     r[RC::B2_V] = V;
+    r[RC::B2_SP] = st.wind ? R(1) : R(0);
     store_rec<RC::B2>(a.rec_b2, s, r);
     a.Vs[s] = V;
+    static_cast<R*>(a.c.Vgws)[s] = Vgw;
     if (a.V_out) a.V_out[a.c.perm[s]] = V;
   }
 };
@@ -114,6 +125,7 @@ template <class R> struct PassB2 {
   struct State {
     R x[RC::XW];
     R ih, L, halfL, V;
+    bool wind;
     Acc<R> m0;
     R m1[3], m2[6], S0[3], S2[6], S3[10];
   };
@@ -123,6 +135,7 @@ template <class R> struct PassB2 {
 #pragma unroll
     for (int k = 0; k < RC::XW; ++k) st.x[k] = r[k];
     st.V = r[RC::B2_V];
+    st.wind = r[RC::B2_SP] != R(0);
     st.ih = R(1) / a.hs[s];
     double L = a.c.box_L[a.c.boxid[s]];
     st.L = (R)L;
@@ -139,6 +152,7 @@ template <class R> struct PassB2 {
   __device__ static const R* src1(const Args&) { return nullptr; }
   __device__ static void pair_s(const Args& a, State& st, const R* r, const R*, uint32_t j,
                                 uint32_t) {
+    if (r[RC::B2_SP] != R(0)) return;  // the corrections reproduce over the gas
     R d[3];
     separation(st.x, r, st.L, st.halfL, d);
     R W, g;
@@ -157,7 +171,7 @@ template <class R> struct PassB2 {
     for (int k = 0; k < 10; ++k) st.S3[k] += gv * xxx[k];
   }
   __device__ static void end(const Args& a, int64_t s, State& st) {
-    st.m0.add(st.V * wendland0(st.ih));
+    if (!st.wind) st.m0.add(st.V * wendland0(st.ih));
     R mom[kMomW];
     mom[0] = st.m0.s;
 #pragma unroll
@@ -169,7 +183,7 @@ template <class R> struct PassB2 {
     R C[16];
     bool sing = rk_coefficients<R>(mom, C);
     store_rec<kMomW>(a.mom, s, mom);
-    if (sing) {
+    if (sing && !st.wind) {  // a wind particle far from gas falls back silently
       atomicAdd(&a.c.hdr->nsingular, 1ull);
       set_status(a.c.hdr, CRK_ESINGULAR);
     }
@@ -190,7 +204,8 @@ template <class R>
 __global__ void k_pack_c1(const R* __restrict__ xs, const R* __restrict__ Vs,
                           const R* __restrict__ ms, const R* __restrict__ v,
                           const R* __restrict__ u, const int32_t* __restrict__ perm, int64_t n,
-                          R* __restrict__ rec, R* __restrict__ us) {
+                          R* __restrict__ rec, R* __restrict__ us, const R* __restrict__ Vgws,
+                          const uint8_t* __restrict__ spec) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   using RC = Rec<R>;
@@ -201,6 +216,7 @@ __global__ void k_pack_c1(const R* __restrict__ xs, const R* __restrict__ Vs,
   const int64_t p = perm[s];
   r[RC::C1_V] = Vs[s];
   r[RC::C1_M] = ms[s];
+  r[RC::C1_VGW] = (spec && spec[s]) ? -Vgws[s] : Vgws[s];
 #pragma unroll
   for (int k = 0; k < 3; ++k) r[RC::C1_VEL + k] = v[k * n + p];
   us[s] = u[p];
@@ -234,7 +250,8 @@ template <class R> struct PassC1 {
   };
   struct State {
     R x[RC::XW];
-    R ih, L, halfL, V, m, v[3];
+    R ih, L, halfL, V, Vgw, m, v[3];
+    bool wind;
     R C[16];
     Acc<R> num, den;
     R gv[9];
@@ -245,6 +262,8 @@ template <class R> struct PassC1 {
 #pragma unroll
     for (int k = 0; k < RC::XW; ++k) st.x[k] = r[k];
     st.V = r[RC::C1_V];
+    st.wind = r[RC::C1_VGW] < R(0);
+    st.Vgw = fabs(r[RC::C1_VGW]);
     st.m = r[RC::C1_M];
 #pragma unroll
     for (int k = 0; k < 3; ++k) st.v[k] = r[RC::C1_VEL + k];
@@ -270,8 +289,13 @@ template <class R> struct PassC1 {
     const R WR = st.C[0] * (R(1) + (st.C[1] * d[0] + st.C[2] * d[1] + st.C[3] * d[2])) * W;
     R G[3];
     rk_gradient(st.C, d, W, g, true, G);
-    st.num.add(r[RC::C1_M] * Vj * WR);
-    st.den.add(Vj * Vj * WR);
+    // density over gas and wind with their volume (Eq. rhow); velocity
+    // gradient over the gas (Eq. gradv)
+    const R vgw = r[RC::C1_VGW];
+    const R Vw = fabs(vgw);
+    st.num.add(r[RC::C1_M] * Vw * WR);
+    st.den.add(Vw * Vw * WR);
+    if (!(vgw > R(0))) return;
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
       const R t = Vj * (st.v[p] - r[RC::C1_VEL + p]);
@@ -281,8 +305,8 @@ template <class R> struct PassC1 {
   }
   __device__ static void end(const Args& a, int64_t s, State& st) {
     const R WR0 = st.C[0] * wendland0(st.ih);
-    st.num.add(st.m * st.V * WR0);
-    st.den.add(st.V * st.V * WR0);
+    st.num.add(st.m * st.Vgw * WR0);
+    st.den.add(st.Vgw * st.Vgw * WR0);
     const R rho = st.num.s / st.den.s;
     const R u = a.us[s];
     const R P = a.gm1 * rho * u;
@@ -299,7 +323,8 @@ template <class R> struct PassC1 {
     r[RC::C2_P] = P;
     r[RC::C2_QA] = a.Cl * rho * cs;
     r[RC::C2_QB] = a.Cq * rho;
-    r[RC::C2_FLAG] = flag ? R(1) : R(0);
+    // 0: corrected, 1: relaxed (App. A.1), 2: wind (no hydro force)
+    r[RC::C2_FLAG] = st.wind ? R(2) : (flag ? R(1) : R(0));
 #pragma unroll
     for (int k = 0; k < 3; ++k) r[RC::C2_VEL + k] = st.v[k];
 #pragma unroll
@@ -359,6 +384,7 @@ template <class R> struct PassC2 {
   __device__ static const R* src1(const Args&) { return nullptr; }
   __device__ static void pair_s(const Args& a, State& st, const R* rj, const R*, uint32_t,
                                 uint32_t) {
+    if (a.c.spec && (st.ri[RC::C2_FLAG] > R(1.5) || rj[RC::C2_FLAG] > R(1.5))) return;  // winds
     R d[3];
     separation(st.ri, rj, st.L, st.halfL, d);
     const R r2 = dot3(d, d);
@@ -408,7 +434,8 @@ crk_status moments_impl(Plan* plan, cudaStream_t st, char* ws, const R* m, R* V_
   const R* hs = reinterpret_cast<const R*>(ws + Ly.hs);
   {
     Phase ph(plan, st, "pack_b1", 1);
-    k_pack_b1<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xs, m, c.perm, n, rec_b1, ms);
+    k_pack_b1<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xs, m, c.perm, n, rec_b1, ms,
+                                                               c.spec);
   }
   typename PassB1<R>::Args a1{c, rec_b1, hs, rec_b2, reinterpret_cast<R*>(ws + Ly.Vs), V_out};
   launch_sweep<PassB1<R>>(plan, st, a1, "b1_volume");
@@ -434,7 +461,8 @@ crk_status rates_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R
     Phase ph(plan, st, "pack_c1", 1);
     k_pack_c1<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
         reinterpret_cast<const R*>(ws + Ly.xs), reinterpret_cast<const R*>(ws + Ly.Vs),
-        reinterpret_cast<const R*>(ws + Ly.ms), v, u, c.perm, n, rec_c1, us);
+        reinterpret_cast<const R*>(ws + Ly.ms), v, u, c.perm, n, rec_c1, us,
+        reinterpret_cast<const R*>(ws + Ly.Vgws), c.spec);
   }
   typename PassC1<R>::Args a1{c,
                               rec_c1,
@@ -483,7 +511,8 @@ crk_status forward_state_impl(Plan* plan, cudaStream_t st, char* ws, const R* v,
     Phase ph(plan, st, "pack_c1", 1);
     k_pack_c1<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
         reinterpret_cast<const R*>(ws + Ly.xs), reinterpret_cast<const R*>(ws + Ly.Vs),
-        reinterpret_cast<const R*>(ws + Ly.ms), v, u, c.perm, n, rec_c1, us);
+        reinterpret_cast<const R*>(ws + Ly.ms), v, u, c.perm, n, rec_c1, us,
+        reinterpret_cast<const R*>(ws + Ly.Vgws), c.spec);
   }
   typename PassC1<R>::Args a3{c, rec_c1, hs, reinterpret_cast<const R*>(ws + Ly.coef), us,
                               reinterpret_cast<R*>(ws + Ly.rec_c2),
@@ -528,7 +557,7 @@ template <class R>
 __global__ void k_pack_state_b(const uint8_t* __restrict__ flg, const int32_t* __restrict__ perm,
                                int64_t n, const R* __restrict__ xs, const R* __restrict__ V_state,
                                const R* __restrict__ coef_state, R* __restrict__ rec_b2,
-                               R* __restrict__ Vs, R* __restrict__ coef) {
+                               R* __restrict__ Vs, R* __restrict__ coef, R* __restrict__ Vgws) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || (flg[s] & 2)) return;
   using RC = Rec<R>;
@@ -541,6 +570,7 @@ __global__ void k_pack_state_b(const uint8_t* __restrict__ flg, const int32_t* _
   r[RC::B2_V] = V;
   store_rec<RC::B2>(rec_b2, s, r);
   Vs[s] = V;
+  Vgws[s] = V;  // no winds in the active-set evaluation
   R C[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) C[k] = coef_state[k * n + p];
@@ -625,9 +655,9 @@ crk_status moments_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* m
   const R* hs = reinterpret_cast<const R*>(ws + Ly.hs);
   {
     Phase ph(plan, st, "pack_b1", 2);
-    k_pack_b1<R><<<g, 256, 0, st>>>(xs, m, c.perm, n, rec_b1, ms);
+    k_pack_b1<R><<<g, 256, 0, st>>>(xs, m, c.perm, n, rec_b1, ms, nullptr);
     k_pack_state_b<R><<<g, 256, 0, st>>>(flg, c.perm, n, xs, V_state, coef_state, rec_b2, Vs,
-                                         coef);
+                                         coef, reinterpret_cast<R*>(ws + Ly.Vgws));
   }
   Common cr = c;
   cr.items = items_r;
@@ -657,7 +687,8 @@ crk_status rates_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, 
     Phase ph(plan, st, "pack_c1", 2);
     k_pack_c1<R><<<g, 256, 0, st>>>(
         reinterpret_cast<const R*>(ws + Ly.xs), reinterpret_cast<const R*>(ws + Ly.Vs),
-        reinterpret_cast<const R*>(ws + Ly.ms), v, u, c.perm, n, rec_c1, us);
+        reinterpret_cast<const R*>(ws + Ly.ms), v, u, c.perm, n, rec_c1, us,
+        reinterpret_cast<const R*>(ws + Ly.Vgws), c.spec);
     k_pack_state_c2<R><<<g, 256, 0, st>>>(
         reinterpret_cast<const uint8_t*>(ws + Ly.flg), c.perm, n,
         reinterpret_cast<const R*>(ws + Ly.xs), reinterpret_cast<const R*>(ws + Ly.hs),
@@ -766,6 +797,43 @@ template crk_status time_bins_impl<float>(Plan*, cudaStream_t, char*, const floa
                                           int64_t, uint8_t*, uint8_t*);
 template crk_status time_bins_impl<double>(Plan*, cudaStream_t, char*, const double*, double, int,
                                            int64_t, uint8_t*, uint8_t*);
+
+// species of the sorted particles (0 gas, nonzero wind) from the caller's order
+__global__ void k_species(const uint8_t* __restrict__ species, const int32_t* __restrict__ perm,
+                          int64_t n, uint8_t* __restrict__ spec) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) spec[s] = species[perm[s]] != 0 ? 1 : 0;
+}
+
+crk_status species_impl(Plan* plan, cudaStream_t st, char* ws, const uint8_t* species) {
+  const int64_t n = plan->ly.n;
+  if (n == 0) return CRK_OK;
+  Phase ph(plan, st, "species", 1);
+  k_species<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      species, reinterpret_cast<const int32_t*>(ws + plan->ly.perm), n,
+      reinterpret_cast<uint8_t*>(ws + plan->ly.spec));
+  return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
+}
+
+template <class R>
+__global__ void k_unsort(const R* __restrict__ in, const int32_t* __restrict__ perm, int64_t n,
+                         R* __restrict__ out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) out[perm[s]] = in[s];
+}
+
+template <class R>
+crk_status volume_gw_impl(Plan* plan, cudaStream_t st, char* ws, R* out) {
+  const int64_t n = plan->ly.n;
+  if (n == 0) return CRK_OK;
+  Phase ph(plan, st, "volume_gw", 1);
+  k_unsort<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<const R*>(ws + plan->ly.Vgws),
+      reinterpret_cast<const int32_t*>(ws + plan->ly.perm), n, out);
+  return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
+}
+template crk_status volume_gw_impl<float>(Plan*, cudaStream_t, char*, float*);
+template crk_status volume_gw_impl<double>(Plan*, cudaStream_t, char*, double*);
 
 template crk_status moments_active_impl<float>(Plan*, cudaStream_t, char*, const float*,
                                                const uint8_t*, float*, float*);

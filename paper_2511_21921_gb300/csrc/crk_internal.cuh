@@ -28,6 +28,7 @@ struct Plan {
   bool has_moments = false;
   bool has_rates = false;
   bool active_moments = false;  // the last moments call was an active-set one
+  bool species = false;         // the workspace holds species (winds) for this build
   bool sorted_keys_in_key0 = true;
   const void* ws_built = nullptr;
   int64_t n = 0;
@@ -80,6 +81,8 @@ crk_status rates_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, 
 template <class R>
 crk_status time_bins_impl(Plan* plan, cudaStream_t st, char* ws, const R* dt, double dt_max,
                           int max_level, int64_t substep, uint8_t* level_out, uint8_t* flags_out);
+crk_status species_impl(Plan* plan, cudaStream_t st, char* ws, const uint8_t* species);
+template <class R> crk_status volume_gw_impl(Plan* plan, cudaStream_t st, char* ws, R* out);
 crk_status leaf_mark_impl(Plan* plan, cudaStream_t st, char* ws, uint8_t* flags,
                           int32_t* leaf_out);
 template <class R>

@@ -39,6 +39,7 @@ template <class R> struct SubArgs {
   const R* Vs;
   const int32_t* boxid;
   const int32_t* perm;
+  const uint8_t* spec;  // nullptr: all gas; winds are skipped (they are subgrid particles)
   const float* aabb;
   const float* hmaxn;
   const int32_t* brange;
@@ -138,7 +139,7 @@ __device__ bool walk(const SubArgs<R>& a, int32_t b, const double* p, double L, 
       const int64_t j0 = (int64_t)(node - a.ni) * kBucket;
       const int64_t j1 = j0 + kBucket < a.n_g ? j0 + kBucket : a.n_g;
       for (int64_t j = j0; j < j1; ++j) {
-        if (a.boxid[j] != b) continue;
+        if (a.boxid[j] != b || (a.spec && a.spec[j])) continue;
         R xj[XW], d[3];
         gas_x(a.xs, a.n_g, j, xj);
         separation(xq, xj, LR, hLR, d);
@@ -243,6 +244,7 @@ static SubArgs<R> sub_args(Plan* P, char* ws, int64_t n_s, const int64_t* box_of
   a.Vs = reinterpret_cast<const R*>(ws + Ly.Vs);
   a.boxid = reinterpret_cast<const int32_t*>(ws + Ly.boxid);
   a.perm = reinterpret_cast<const int32_t*>(ws + Ly.perm);
+  a.spec = P->species ? reinterpret_cast<const uint8_t*>(ws + Ly.spec) : nullptr;
   a.aabb = reinterpret_cast<const float*>(ws + Ly.aabb);
   a.hmaxn = reinterpret_cast<const float*>(ws + Ly.hmaxn);
   a.brange = reinterpret_cast<const int32_t*>(ws + Ly.brange);

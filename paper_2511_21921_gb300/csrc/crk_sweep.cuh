@@ -23,6 +23,10 @@ struct Common {
   // warps then take 32 listed particles per item instead of 32 consecutive ones
   const int32_t* items = nullptr;
   const int32_t* n_items = nullptr;
+  // species of the sorted particles (nullptr: all gas) and the volume over
+  // gas and wind the volume sweep writes
+  const uint8_t* spec = nullptr;
+  void* Vgws = nullptr;
 };
 
 // Ask L1 for the cache lines of neighbor j's record (base + j*bytes, `bytes`
@@ -49,6 +53,8 @@ inline Common make_common(const Plan* plan, char* ws) {
   c.perm = reinterpret_cast<const int32_t*>(ws + Ly.perm);
   c.cap_pp = Ly.cap_pp;
   c.pf = plan->p.prefetch;
+  c.spec = plan->species ? reinterpret_cast<const uint8_t*>(ws + Ly.spec) : nullptr;
+  c.Vgws = ws + Ly.Vgws;
   return c;
 }
 

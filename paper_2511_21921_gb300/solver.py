@@ -158,6 +158,18 @@ class Solver:
                 "crk_adjoint")
         return gx, gv, gu, gh
 
+    # -- gas and wind ----------------------------------------------------------------
+    def set_species(self, species):
+        """Species of the last build's particles (uint8, 0 gas, nonzero wind);
+        None returns to all gas.  Call after every cell_build."""
+        L.check(L.crk_set_species(self.plan, _stream(), self._wsp, _ptr(species)),
+                "crk_set_species")
+
+    def volume_gw(self):
+        out = torch.empty(self.n, dtype=self.dtype, device=self.device)
+        L.check(L.crk_volume_gw(self.plan, _stream(), self._wsp, out.data_ptr()), "crk_volume_gw")
+        return out
+
     # -- active-set evaluation (passive particles reuse their stored fields) -------
     def leaf_mark(self, flags, want_leaf=False):
         """Set bit 1 on the leaf-mates of transformed particles (bit 2), in place."""
@@ -357,8 +369,10 @@ class Solver:
         return g
 
     # -- one call for the whole forward path ------------------------------------
-    def forward(self, x, h, m, v, u, box_off=None, box_L=None, L_box=1.0, **want):
+    def forward(self, x, h, m, v, u, box_off=None, box_L=None, L_box=1.0, species=None, **want):
         self.cell_build(x, h, box_off, box_L, L_box)
+        if species is not None:
+            self.set_species(species)
         V, coef = self.moments(m, want.get("want_V", False), want.get("want_coef", False))
         dvdt, dudt, rho, gv = self.rates(v, u, want.get("want_rho", False),
                                          want.get("want_gradv", False))
