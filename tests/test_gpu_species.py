@@ -75,3 +75,34 @@ def test_no_winds_is_bitwise_the_gas_path_and_guards():
     rc = L.crk_adjoint(s.plan, 0, s._wsp, t["v"].data_ptr(), t["u"].data_ptr(), z3.data_ptr(),
                        z.data_ptr(), z3.data_ptr(), z3.data_ptr(), z.data_ptr(), z.data_ptr(), 1)
     assert rc == L.CRK_ESTATE
+
+
+def test_subgrid_sums_skip_winds():
+    """Winds are subgrid particles: the scatter volume and the deposits of
+    other subgrid particles run over the gas only (App. A.2)."""
+    from oracle import subgrid as S
+    d, sp = _winds(5, n_side=16, frac=0.1)
+    n = d["h"].shape[0]
+    t = to_dev(d, "fp64")
+    s = Solver(n, 1, "fp64")
+    s.cell_build(t["x"], t["h"])
+    s.set_species(torch.tensor(sp, device="cuda"))
+    Vg, _ = s.moments(t["m"], want_V=True)
+    rng = np.random.default_rng(6)
+    xs = rng.uniform(0, 1, (3, 50))
+    hs = rng.uniform(0.08, 0.15, 50)
+    xs_d = torch.tensor(xs, device="cuda")
+    hs_d = torch.tensor(hs, device="cuda")
+    V, _ = s.subgrid_volume(xs_d, hs_d, want_h=False)
+    q = np.ones((1, 50))
+    dq, A = s.subgrid_deposit(xs_d, hs_d, torch.tensor(q, device="cuda"))
+    torch.cuda.synchronize()
+    assert s.poll() == 0
+    gas = sp == 0
+    eV, _ = S.volume(xs, hs, d["x"][:, gas], d["h"][gas])
+    assert np.allclose(V.cpu().numpy(), eV, rtol=1e-12)
+    edq, eA = S.deposit(xs, hs, q, d["x"][:, gas], Vg.cpu().numpy()[gas])
+    got = dq.cpu().numpy()
+    assert np.all(got[:, ~gas] == 0)
+    assert np.allclose(got[:, gas], edq, rtol=1e-12, atol=1e-15)
+    assert np.allclose(A.cpu().numpy(), eA, rtol=1e-12)
