@@ -43,8 +43,9 @@ def _digest() -> str:
     h = hashlib.sha256()
     files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh")))
     files += [os.path.join(INCLUDE, "crk.h"), os.path.abspath(__file__)]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     for f in files:
-        h.update(f.encode())
+        h.update(os.path.relpath(f, root).encode())  # independent of where the tree lives
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
