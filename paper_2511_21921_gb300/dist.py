@@ -4,6 +4,12 @@ Boxes are independent problems, so N ranks need no data-path collective: each
 rank takes a set of whole boxes (balanced by particle count) and runs them in
 one batched call; a single-box workload is replicated (weak scaling).  The only
 collective is the max over ranks of the step time.
+
+``overload_slabs`` is the paper's "overloading" decomposition of one box (Sec.
+2.1: particles near a domain boundary are duplicated in the adjacent domain, so
+each domain evaluates its own particles without communication): slabs of the
+box along one axis, each with the ghost particles its owned particles' rates
+depend on.
 """
 from __future__ import annotations
 
@@ -64,3 +70,68 @@ def sum_over_ranks(value: float, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def _union_neighbors(tree, x, h, hmax, idx, L):
+    """Indices j with |x_ij| < max(h_i, h_j) for i in idx (minimum image)."""
+    out = set()
+    cand = tree.query_ball_point(x[idx], np.maximum(h[idx], hmax))
+    for i, cs in zip(idx, cand):
+        if not cs:
+            continue
+        cs = np.asarray(cs)
+        d = x[cs] - x[i]
+        d -= L * np.round(d / L)
+        r = np.sqrt((d * d).sum(axis=1))
+        keep = cs[(r < h[i]) | (r < h[cs])]
+        out.update(keep.tolist())
+    return out
+
+
+def overload_slabs(x, h, n_slabs, L=1.0, axis=0, union_csr=None):
+    """Split a periodic box into ``n_slabs`` slabs along ``axis`` and give each
+    the ghosts its owned particles need: the rates of i read the fields of its
+    union neighbors j, whose density, gradient and coefficients read their own
+    neighbors' volumes, which read theirs -- three levels of union neighbors.
+    With those ghosts present the owned particles' rates are those of the whole
+    box (up to summation order).  x: (3, n); h: (n,).  Returns a list of
+    (owned, ghosts) index arrays, one pair per slab; owned sets partition the box.
+    union_csr: optional (row_ptr, col) of the union neighbor sets (as
+    crk_neighbors_csr gives them); the closure is then three sparse products
+    instead of k-d tree queries.
+    """
+    x = np.asarray(x, dtype=np.float64).T.copy()
+    h = np.asarray(h, dtype=np.float64)
+    n = h.shape[0]
+    slab = np.minimum((x[:, axis] / L * n_slabs).astype(np.int64), n_slabs - 1)
+    if union_csr is not None:
+        from scipy.sparse import csr_matrix
+        row, col = (np.asarray(a) for a in union_csr)
+        A = csr_matrix((np.ones(col.size, dtype=np.int32), col, row), shape=(n, n))
+        A = ((A + A.T) > 0).astype(np.int32)   # union sets are symmetric; be safe
+        out = []
+        for s in range(n_slabs):
+            reach = (slab == s)
+            owned = np.nonzero(reach)[0]
+            for _ in range(3):
+                reach = reach | (A @ reach.astype(np.int32) > 0)
+            ghosts = np.nonzero(reach & (slab != s))[0]
+            out.append((owned, ghosts))
+        return out
+    from scipy.spatial import cKDTree
+    tree = cKDTree(np.mod(x, L), boxsize=L)
+    hmax = float(h.max()) if n else 0.0
+    out = []
+    for s in range(n_slabs):
+        owned = np.nonzero(slab == s)[0]
+        need = set(owned.tolist())
+        frontier = owned
+        for _ in range(3):
+            nxt = _union_neighbors(tree, x, h, hmax, frontier, L) - need
+            need |= nxt
+            frontier = np.fromiter(nxt, dtype=np.int64, count=len(nxt))
+            if frontier.size == 0:
+                break
+        ghosts = np.array(sorted(need - set(owned.tolist())), dtype=np.int64)
+        out.append((owned, ghosts))
+    return out

@@ -60,3 +60,37 @@ def test_single_box_is_replicated():
     d = synth.lattice(8, seed=1)
     for r in range(3):
         assert D.shard_workload(d, r, 3) is d
+
+
+def test_overload_slabs_partition_and_closure():
+    """Owned sets partition the box; each slab's ghosts hold every particle
+    within three levels of union neighbors of its owned particles (brute force)."""
+    import numpy as np
+    from paper_2511_21921_gb300 import dist as D
+    rng = np.random.default_rng(0)
+    n = 600
+    x = rng.uniform(0, 1, (3, n))
+    h = rng.uniform(0.05, 0.12, n)
+    parts = D.overload_slabs(x, h, 3)
+    owned = np.concatenate([o for o, _ in parts])
+    assert np.array_equal(np.sort(owned), np.arange(n))
+    d = x[:, :, None] - x[:, None, :]
+    d -= np.round(d)
+    r = np.sqrt((d * d).sum(0))
+    adj = (r < np.maximum(h[:, None], h[None, :]))
+    for o, g in parts:
+        reach = np.zeros(n, bool)
+        reach[o] = True
+        for _ in range(3):
+            reach = reach | adj[reach].any(axis=0)
+        have = np.zeros(n, bool)
+        have[o] = True
+        have[g] = True
+        assert np.array_equal(reach, have)
+        assert not np.intersect1d(o, g).size
+    # the same closure from union neighbor sets given as CSR
+    rows = [np.nonzero(adj[i] & (np.arange(n) != i))[0] for i in range(n)]
+    rp = np.concatenate([[0], np.cumsum([len(c) for c in rows])])
+    parts2 = D.overload_slabs(x, h, 3, union_csr=(rp, np.concatenate(rows)))
+    for (o1, g1), (o2, g2) in zip(parts, parts2):
+        assert np.array_equal(o1, o2) and np.array_equal(g1, g2)
