@@ -73,7 +73,9 @@ typedef enum {
   CRK_ENONFINITE = 5,  /* NaN or Inf in an input */
   CRK_ESINGULAR = 6,   /* second moment m2 singular for some particle (it falls back to A=1, B=0) */
   CRK_ETIMEOUT = 7,    /* a bounded device wait gave up */
-  CRK_ESTATE = 8       /* call out of order (e.g. crk_rates before crk_moments) */
+  CRK_ESTATE = 8,      /* call out of order (e.g. crk_rates before crk_moments) */
+  CRK_EBOUNDS = 9      /* bounds-checked build only: a kernel met an index out of range
+                          (the access was skipped; outputs are undefined) */
 } crk_status;
 
 typedef enum {

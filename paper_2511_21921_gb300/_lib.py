@@ -13,11 +13,12 @@ import re
 from . import build as _build
 
 CRK_OK, CRK_EINVAL, CRK_ENOMEM, CRK_ECUDA, CRK_EDOMAIN, CRK_ENONFINITE, CRK_ESINGULAR, \
-    CRK_ETIMEOUT, CRK_ESTATE = range(9)
+    CRK_ETIMEOUT, CRK_ESTATE, CRK_EBOUNDS = range(10)
 CRK_FP64, CRK_MIXED32 = 0, 1
 
 STATUS_NAMES = {0: "CRK_OK", 1: "CRK_EINVAL", 2: "CRK_ENOMEM", 3: "CRK_ECUDA", 4: "CRK_EDOMAIN",
-                5: "CRK_ENONFINITE", 6: "CRK_ESINGULAR", 7: "CRK_ETIMEOUT", 8: "CRK_ESTATE"}
+                5: "CRK_ENONFINITE", 6: "CRK_ESINGULAR", 7: "CRK_ETIMEOUT", 8: "CRK_ESTATE",
+                9: "CRK_EBOUNDS"}
 
 
 class crk_params(C.Structure):
@@ -100,13 +101,16 @@ _lib = None
 
 
 def load(build_if_missing: bool = True) -> C.CDLL:
-    """Load libcrk.so (building it first when allowed); raises if unavailable."""
+    """Load libcrk.so (building it first when allowed); raises if unavailable.
+    With CRK_BOUNDS_CHECK=1 in the environment the bounds-checked build is
+    loaded instead."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    bc = os.environ.get("CRK_BOUNDS_CHECK", "0") == "1"
+    path = _build.LIB_BC if bc else _build.LIB
     if build_if_missing:
-        path = _build.build_library()
+        path = _build.build_library(bounds_check=bc)
     if not os.path.exists(path):
         raise ImportError(f"libcrk.so not built at {path}; run paper_2511_21921_gb300.build")
     lib = C.CDLL(path)

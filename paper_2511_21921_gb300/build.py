@@ -18,6 +18,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcrk.so")
+# Bounds-checked variant: every neighbor index, list slot and tree node a kernel
+# reads is checked first; a bad one sets CRK_EBOUNDS in the device status word
+# and the access is skipped.  Same arithmetic otherwise.
+LIB_BC = os.path.join(OUT_DIR, "libcrk_bc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Single-precision division and square root to within 2 ulp, subnormals flushed
@@ -51,21 +55,25 @@ def _digest() -> str:
     return h.hexdigest()
 
 
-def build_library(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libcrk.so unless an up-to-date build exists."""
+def build_library(force: bool = False, verbose: bool = False, bounds_check: bool = False) -> str:
+    """Compile and link libcrk.so (or the bounds-checked libcrk_bc.so) unless an
+    up-to-date build exists."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    stamp = os.path.join(OUT_DIR, "libcrk.stamp")
+    lib = LIB_BC if bounds_check else LIB
+    tag = "bc" if bounds_check else ""
+    stamp = os.path.join(OUT_DIR, f"libcrk{tag}.stamp")
     dg = _digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    if not force and os.path.exists(lib) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read().strip() == dg:
-                return LIB
+                return lib
     nvcc = _nvcc()
     objs = []
+    extra = ["-DCRK_BOUNDS_CHECK=1"] if bounds_check else []
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *NVCC_FLAGS, *ARCH, "-c", src, "-o", obj]
+        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + f"{tag}.o")
+        cmd = [nvcc, *NVCC_FLAGS, *extra, *ARCH, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -75,15 +83,15 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as fh:
         fh.write(dg)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

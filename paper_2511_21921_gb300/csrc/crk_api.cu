@@ -4,6 +4,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "crk_internal.cuh"
 
 namespace crk {
@@ -117,8 +119,12 @@ static crk_status check_ws(const Plan& P, const void* ws) {
   return CRK_OK;
 }
 
+// Every phase is an NVTX range (named like its timing record) for profilers
+// that attach to the process; without one the push and pop are no-ops.
 Phase::Phase(Plan* plan, cudaStream_t s, const char* name, int kernels) : p(plan), st(s) {
   p->launches += kernels;
+  nvtxRangePushA(name);
+  range = true;
   if (!p->timing || p->n_timed >= Plan::kMaxTimed) return;
   if (!p->ev_ready) {
     for (int k = 0; k < 2 * Plan::kMaxTimed; ++k) cudaEventCreate(&p->ev[k]);
@@ -132,6 +138,8 @@ Phase::Phase(Plan* plan, cudaStream_t s, const char* name, int kernels) : p(plan
 void Phase::end() {
   if (slot >= 0) cudaEventRecord(p->ev[2 * slot + 1], st);
   slot = -1;
+  if (range) nvtxRangePop();
+  range = false;
 }
 
 }  // namespace crk
@@ -586,6 +594,7 @@ const char* crk_status_string(crk_status s) {
     case CRK_ESINGULAR: return "singular second moment (uncorrected kernel used)";
     case CRK_ETIMEOUT: return "bounded device wait gave up";
     case CRK_ESTATE: return "call out of order or workspace not built";
+    case CRK_EBOUNDS: return "index out of range (bounds-checked build)";
   }
   return "unknown status";
 }

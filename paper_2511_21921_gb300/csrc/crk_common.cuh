@@ -51,6 +51,25 @@ __device__ __forceinline__ void set_status(DevHeader* h, int code) {
   atomicCAS(&h->status, 0, code);
 }
 
+// Bounds-checked build (-DCRK_BOUNDS_CHECK=1): an index a kernel is about to
+// follow is checked against its array length; a bad one records CRK_EBOUNDS
+// (the status code; see crk.h) and the caller skips the access.  A no-op
+// otherwise.
+#ifndef CRK_BOUNDS_CHECK
+#define CRK_BOUNDS_CHECK 0
+#endif
+__device__ __forceinline__ bool index_ok(DevHeader* h, int64_t i, int64_t n) {
+#if CRK_BOUNDS_CHECK
+  if (i < 0 || i >= n) {
+    atomicCAS(&h->status, 0, 9);
+    return false;
+  }
+#else
+  (void)h; (void)i; (void)n;
+#endif
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // precision traits: float records carry positions as double-float (hi, lo)
 // pairs (6 words); double records carry them as plain doubles (3 words).

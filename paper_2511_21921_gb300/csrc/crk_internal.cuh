@@ -50,6 +50,7 @@ struct Phase {
   Plan* p;
   cudaStream_t st;
   int slot = -1;
+  bool range = false;  // an NVTX range is open
   Phase(Plan* plan, cudaStream_t s, const char* name, int kernels);
   void end();  // record the stop event now (idempotent)
   ~Phase() { end(); }

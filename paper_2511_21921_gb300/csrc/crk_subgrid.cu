@@ -107,9 +107,10 @@ __device__ bool walk(const SubArgs<R>& a, int32_t b, const double* p, double L, 
   const R LR = (R)L, hLR = (R)(0.5 * L);
   while (sp > 0) {
     const int take = sp < 32 ? sp : 32;
-    const int32_t node = lane < take ? stk[sp - take + lane] : -1;
+    int32_t node = lane < take ? stk[sp - take + lane] : -1;
     sp -= take;
     __syncwarp();
+    if (node >= 0 && !index_ok(a.hdr, node, a.nt)) node = -1;
     bool ov = false;
     if (node >= 0 && b >= a.brange[node] && b <= a.brange[a.nt + node]) {
       const float R_ = (reach_fixed >= 0.f ? reach_fixed : a.hmaxn[node]) * 1.00001f + 1e-6f * Lf;

@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
     if (a.c.items) {
       live = s < nlist;
       s = live ? a.c.items[s] : 0;
+      if (live && !index_ok(a.c.hdr, s, a.c.n)) live = false, s = 0;
     }
     typename P::State st;
     int lg = 0, ls = 0;
@@ -164,16 +165,20 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
         const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
         return __ldg(col + slot * 32);
       };
-      uint32_t e_next = tot > 0 ? entry(0) : 0u;
+      // a bad entry (bounds-checked build only) is redirected to the particle itself
+      auto safe = [&](uint32_t e) -> uint32_t {
+        return index_ok(a.c.hdr, e & kIdxMask, a.c.n) ? e : (uint32_t)s;
+      };
+      uint32_t e_next = tot > 0 ? safe(entry(0)) : 0u;
       if (tot > 0) Stage<P>::issue(a, ring, 0, e_next & kIdxMask);
       cp_async_commit();
-      uint32_t e_after = tot > 1 ? entry(1) : 0u;
+      uint32_t e_after = tot > 1 ? safe(entry(1)) : 0u;
       for (int k = 0; k < wmax; ++k) {
         const uint32_t e = e_next;
         e_next = e_after;
         if (k + 1 < tot) Stage<P>::issue(a, ring, (k + 1) & 1, e_next & kIdxMask);
         cp_async_commit();
-        e_after = k + 2 < tot ? entry(k + 2) : 0u;
+        e_after = k + 2 < tot ? safe(entry(k + 2)) : 0u;
         cp_async_wait<1>();
         if (k < tot) {
           Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
         if (pf && k + pf < lg)
           prefetch_sources<P>(a, __ldg(col + (int64_t)(k + pf) * 32) & kIdxMask);
         const uint32_t e = __ldg(col + (int64_t)k * 32);
-        if (k < lg) {
+        if (k < lg && index_ok(a.c.hdr, e & kIdxMask, a.c.n)) {
           Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
           load_sources<P>(a, e & kIdxMask, r0, r1);
           P::pair_s(a, st, r0, r1, e & kIdxMask, e);
@@ -212,9 +217,11 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
         if (k < tot) {
           const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
           const uint32_t e = __ldg(col + slot * 32);
-          Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
-          load_sources<P>(a, e & kIdxMask, r0, r1);
-          P::pair_s(a, st, r0, r1, e & kIdxMask, e);
+          if (index_ok(a.c.hdr, e & kIdxMask, a.c.n)) {
+            Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
+            load_sources<P>(a, e & kIdxMask, r0, r1);
+            P::pair_s(a, st, r0, r1, e & kIdxMask, e);
+          }
         }
       }
     }
