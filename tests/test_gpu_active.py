@@ -168,3 +168,21 @@ def test_power_of_two_time_bins_per_leaf():
         act = (sub % (2 ** (max_level - k))) == 0
         assert np.array_equal((fl & 1) != 0, act)
         assert np.array_equal(fl & ~np.uint8(1), flags0 & ~np.uint8(1))
+
+
+def test_time_bins_across_boxes_and_ragged_tail():
+    """Levels on a multi-box batch whose size is not a multiple of the leaf
+    size: every particle gets a level, leaves may span a box boundary."""
+    d = synth.multibox(3, seed0=60, nmin=9, nmax=11)
+    n = d["h"].shape[0]
+    t = to_dev(d, "fp64")
+    s = Solver(n, len(d["box_off"]) - 1, "fp64")
+    s.cell_build(t["x"], t["h"], t["box_off"], t["box_L"])
+    dt = torch.full((n,), 0.3, dtype=torch.float64, device="cuda")
+    dt[::7] = 0.01
+    level, flags = s.time_bins(dt, 1.0, 8, 0)
+    lv = level.cpu().numpy().astype(int)
+    assert lv.size == n and lv.min() >= 0 and lv.max() <= 8
+    assert np.all((flags.cpu().numpy() & 1) == 1)   # sub-step 0: every leaf is active
+    dmin = dt.cpu().numpy()
+    assert np.all(1.0 / 2.0 ** lv <= 0.3 + 1e-15)

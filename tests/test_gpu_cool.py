@@ -93,3 +93,14 @@ def test_semigroup_on_gpu_fp64():
     half, _ = _run("fp64", u0, rho, 0.01, lam)
     two, _ = _run("fp64", half, rho, 0.02, lam)
     assert np.allclose(one, two, rtol=1e-10, atol=0)
+
+
+def test_two_node_table_and_pure_heating_fp64():
+    """The smallest table (one bin) and a heating-only table: closed forms."""
+    lam = np.array([-1.5, -1.5])          # constant heating over one bin, 1e-3 .. 1e-3+0.004 dex
+    u0 = np.array([1.0e-3, 1.004e-3, 1.009e-3])
+    got, _ = _run("fp64", u0, np.ones(3), 1e-7, lam)
+    top = 10 ** (LOGU0 + DEX)
+    expect = np.minimum(u0 + 1.5e-7, top)
+    expect[u0 > top] = u0[u0 > top]
+    assert np.allclose(got, expect, rtol=1e-13, atol=0)
