@@ -263,6 +263,26 @@ def run_ours(args, rank, world):
     e2e_ms = timed(e2e_step, max(3, args.steps // 4))
     e2e_mean = sum(e2e_ms) / len(e2e_ms)
 
+    # the same step with the fused rates + adjoint call (cotangents known in
+    # advance): the adjoint's pair sweep also forms the rates
+    fused = None
+    if with_adj and nb == 1:
+        fout = (outs[0], outs[1]) + grads
+
+        def fstep():
+            s.cell_build(dv["x"], dv["h"], *boxes, check=False)
+            s.moments(dv["m"])
+            s.rates_adjoint(dv["v"], dv["u"], dv["ga"], dv["gu"], out=fout)
+        fstep()
+        fgraph = s.capture(fstep) if args.graph else None
+        frun = fgraph.replay if fgraph is not None else fstep
+        for _ in range(2):
+            frun()
+        fms = timed(frun, max(3, min(args.steps, 50)))
+        fmean = sum(fms) / len(fms)
+        fused = {"ms_per_step": round(fmean, 4), "value": pairs / (fmean * 1e-3),
+                 "step": "build+moments+rates_adjoint (fused rates and adjoint sweep)"}
+
     # per-kernel durations (library CUDA events on the launching stream)
     L.crk_timing_enable(s.plan, True)
     kt = {}
@@ -305,6 +325,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": job_pairs / (D.max_over_ranks(e2e_mean, device=dev) * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "fused_rates_adjoint": fused,
         "autotune": {k: v["variant"] for k, v in tuned.items()} if tuned else None,
         "graph": bool(graph is not None),
         "eager_ms_per_step": round(sum(ms_eager) / len(ms_eager), 4),

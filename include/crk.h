@@ -153,6 +153,18 @@ crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void
                        const void* g_dvdt, const void* g_dudt, void* g_x, void* g_v, void* g_u,
                        void* g_h, int32_t recompute);
 
+/* (d') Rates and their vector-Jacobian product in one pass structure, for
+ * cotangents known before the rates (a loss linear in the rates, or lagged
+ * cotangents): the density sweep, then the adjoint's pair sweep accumulates
+ * the forward rates from the same pair forces it differentiates, then the
+ * other reverse sweeps.  Outputs as crk_rates (dvdt, dudt) and crk_adjoint
+ * (g_x, g_v, g_u, g_h); the rates agree with crk_rates' to rounding (the pair
+ * expressions are the same, the compiler may contract them differently).
+ * Requires crk_moments (not the active-set or wind configurations). */
+crk_status crk_rates_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void* v,
+                             const void* u, const void* g_dvdt, const void* g_dudt, void* dvdt,
+                             void* dudt, void* g_x, void* g_v, void* g_u, void* g_h);
+
 /* ---- Gas and wind (Sec. 2.5.1, Eq. rhow; App. A.2) -----------------------------
  * Wind particles live in the same boxes, tree and lists as the gas but take
  * part in the density only: the gas density sums over gas and wind neighbors

@@ -82,6 +82,8 @@ _SIGS = {
     "crk_subgrid_deposit": (C.c_int, [_VP, _VP, _VP, C.c_int64, _VP, _VP, _VP, C.c_int32, _VP,
                                       _VP, _VP, _VP]),
     "crk_set_species": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "crk_rates_adjoint": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                    _VP]),
     "crk_volume_gw": (C.c_int, [_VP, _VP, _VP, _VP]),
     "crk_leaf_mark": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "crk_time_bins": (C.c_int, [_VP, _VP, _VP, _VP, C.c_double, C.c_int32, C.c_int64, _VP, _VP]),
@@ -267,6 +269,13 @@ def crk_subgrid_deposit(plan, stream, ws, n_s, box_off_s, x_s, h_s, n_comp, q_s,
 
 def crk_leaf_mark(plan, stream, ws, flags, leaf_out=None) -> int:
     return load().crk_leaf_mark(_VP(plan), _VP(stream), _VP(ws), _VP(flags), _VP(leaf_out))
+
+
+def crk_rates_adjoint(plan, stream, ws, v, u, g_dvdt, g_dudt, dvdt, dudt, g_x, g_v, g_u,
+                      g_h) -> int:
+    return load().crk_rates_adjoint(_VP(plan), _VP(stream), _VP(ws), _VP(v), _VP(u),
+                                    _VP(g_dvdt), _VP(g_dudt), _VP(dvdt), _VP(dudt), _VP(g_x),
+                                    _VP(g_v), _VP(g_u), _VP(g_h))
 
 
 def crk_set_species(plan, stream, ws, species) -> int:

@@ -241,6 +241,10 @@ template <class R> struct PassA2 {
     R* cbar;
     AVParams<R> av;
     R Cl, Cq, gm1, ggm1;
+    // optional: the forward rates, accumulated from the same pair forces
+    // (the fused forward + adjoint sweep of crk_rates_adjoint)
+    R* dvdt;
+    R* dudt;
   };
   struct State {
     R ri[RC::C2];
@@ -249,6 +253,8 @@ template <class R> struct PassA2 {
     int64_t s;
     R xb[3], vb[3], hb, Vb, Pb, rhob, cb;
     R Cb[16], gvb[9];
+    R fa[3];
+    Acc<R> fe;
   };
   __device__ static void begin(const Args& a, int64_t s, State& st) {
     load_rec<RC::C2>(a.rec_c2, s, st.ri);
@@ -266,6 +272,8 @@ template <class R> struct PassA2 {
     for (int k = 0; k < 16; ++k) st.Cb[k] = R(0);
 #pragma unroll
     for (int k = 0; k < 9; ++k) st.gvb[k] = R(0);
+    st.fa[0] = st.fa[1] = st.fa[2] = R(0);
+    st.fe = Acc<R>();
   }
   __device__ static const R* src0(const Args& a) { return a.rec_c2; }
   __device__ static const R* src1(const Args& a) { return a.rec_ab; }
@@ -334,6 +342,11 @@ template <class R> struct PassA2 {
     for (int p = 0; p < 3; ++p) {
       dG[p] = Gi[p] - Gj[p];
       F[p] = pre * dG[p];
+    }
+    if (a.dvdt) {  // forward rates from the same force (fused sweep)
+#pragma unroll
+      for (int p = 0; p < 3; ++p) st.fa[p] += F[p];
+      st.fe.add(R(-0.5) * (F[0] * vij[0] + F[1] * vij[1] + F[2] * vij[2]));
     }
     // ---- reverse
     const R bsum = st.ab[3] + abj[3];
@@ -434,6 +447,13 @@ template <class R> struct PassA2 {
   }
   __device__ static void end(const Args& a, int64_t s, State& st) {
     using A_ = ARec<R>;
+    if (a.dvdt) {
+      const R im = R(1) / a.ms[s];
+      const int64_t p = a.c.perm[s];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) a.dvdt[k * a.c.n + p] = st.fa[k] * im;
+      a.dudt[p] = st.fe.s * im;
+    }
     const R u = a.us[s];
     // EOS: P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u)
     const R rhob = st.rhob + a.gm1 * u * st.Pb;
@@ -864,7 +884,7 @@ template <class R> struct PassAB1 {
 template <class R>
 crk_status adjoint_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u,
                         const R* g_dvdt, const R* g_dudt, R* g_x, R* g_v, R* g_u, R* g_h,
-                        int recompute) {
+                        int recompute, R* dvdt, R* dudt) {
   const Layout& Ly = plan->ly;
   const int64_t n = Ly.n;
   const crk_params& p = plan->p;
@@ -901,8 +921,10 @@ crk_status adjoint_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const
                               (R)p.Cl,
                               (R)p.Cq,
                               (R)(p.gamma - 1.0),
-                              (R)(p.gamma * (p.gamma - 1.0))};
-  launch_sweep<PassA2<R>>(plan, st, a2, "adj_c2");
+                              (R)(p.gamma * (p.gamma - 1.0)),
+                              dvdt,
+                              dudt};
+  launch_sweep<PassA2<R>>(plan, st, a2, dvdt ? "rates_adj_c2" : "adj_c2");
   typename PassA1<R>::Args a1{c, rec_a1, reinterpret_cast<const R*>(ws + Ly.mom), cbar, rec_a2,
                               acc};
   launch_sweep<PassA1<R>>(plan, st, a1, "adj_c1");
@@ -915,9 +937,9 @@ crk_status adjoint_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const
 
 template crk_status adjoint_impl<float>(Plan*, cudaStream_t, char*, const float*, const float*,
                                         const float*, const float*, float*, float*, float*, float*,
-                                        int);
+                                        int, float*, float*);
 template crk_status adjoint_impl<double>(Plan*, cudaStream_t, char*, const double*, const double*,
                                          const double*, const double*, double*, double*, double*,
-                                         double*, int);
+                                         double*, int, double*, double*);
 
 }  // namespace crk

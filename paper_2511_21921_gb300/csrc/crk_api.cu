@@ -437,6 +437,45 @@ crk_status crk_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void
   return s;
 }
 
+crk_status crk_rates_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, const void* v,
+                             const void* u, const void* g_dvdt, const void* g_dudt, void* dvdt,
+                             void* dudt, void* g_x, void* g_v, void* g_u, void* g_h) {
+  if (!plan) return CRK_EINVAL;
+  Plan& P = plan->impl;
+  crk_status s = check_ws(P, ws);
+  if (s != CRK_OK) return s;
+  if (!P.has_moments || P.active_moments || P.species) return CRK_ESTATE;
+  if (P.n > 0 && (!v || !u || !g_dvdt || !g_dudt || !dvdt || !dudt || !g_x || !g_v || !g_u ||
+                  !g_h))
+    return CRK_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  if (P.p.precision == CRK_FP64) {
+    s = rates_impl<double>(&P, st, w, static_cast<const double*>(v),
+                           static_cast<const double*>(u), nullptr, nullptr, nullptr, nullptr,
+                           false);
+    if (s == CRK_OK)
+      s = adjoint_impl<double>(&P, st, w, static_cast<const double*>(v),
+                               static_cast<const double*>(u), static_cast<const double*>(g_dvdt),
+                               static_cast<const double*>(g_dudt), static_cast<double*>(g_x),
+                               static_cast<double*>(g_v), static_cast<double*>(g_u),
+                               static_cast<double*>(g_h), 0, static_cast<double*>(dvdt),
+                               static_cast<double*>(dudt));
+  } else {
+    s = rates_impl<float>(&P, st, w, static_cast<const float*>(v), static_cast<const float*>(u),
+                          nullptr, nullptr, nullptr, nullptr, false);
+    if (s == CRK_OK)
+      s = adjoint_impl<float>(&P, st, w, static_cast<const float*>(v),
+                              static_cast<const float*>(u), static_cast<const float*>(g_dvdt),
+                              static_cast<const float*>(g_dudt), static_cast<float*>(g_x),
+                              static_cast<float*>(g_v), static_cast<float*>(g_u),
+                              static_cast<float*>(g_h), 0, static_cast<float*>(dvdt),
+                              static_cast<float*>(dudt));
+  }
+  if (s == CRK_OK) P.has_rates = true;
+  return s;
+}
+
 crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
                         const void* v, const void* u, const void* g_dvdt, const void* g_dudt,
                         int32_t repeats, int32_t* choice_out, float* ms_out) {

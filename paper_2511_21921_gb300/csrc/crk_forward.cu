@@ -447,7 +447,7 @@ crk_status moments_impl(Plan* plan, cudaStream_t st, char* ws, const R* m, R* V_
 
 template <class R>
 crk_status rates_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u, R* dvdt,
-                      R* dudt, R* rho_out, R* gradv_out) {
+                      R* dudt, R* rho_out, R* gradv_out, bool do_c2) {
   const Layout& Ly = plan->ly;
   const int64_t n = Ly.n;
   const crk_params& p = plan->p;
@@ -480,9 +480,11 @@ crk_status rates_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R
                               (R)p.Cq,
                               (R)p.relax_dt};
   launch_sweep<PassC1<R>>(plan, st, a1, "c1_density");
-  typename PassC2<R>::Args a2{c, rec_c2, reinterpret_cast<const R*>(ws + Ly.ms), dvdt, dudt,
-                              make_av<R>(p)};
-  launch_sweep<PassC2<R>>(plan, st, a2, "c2_rates");
+  if (do_c2) {
+    typename PassC2<R>::Args a2{c, rec_c2, reinterpret_cast<const R*>(ws + Ly.ms), dvdt, dudt,
+                                make_av<R>(p)};
+    launch_sweep<PassC2<R>>(plan, st, a2, "c2_rates");
+  }
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }
 
@@ -848,8 +850,8 @@ template crk_status moments_impl<float>(Plan*, cudaStream_t, char*, const float*
 template crk_status moments_impl<double>(Plan*, cudaStream_t, char*, const double*, double*,
                                          double*);
 template crk_status rates_impl<float>(Plan*, cudaStream_t, char*, const float*, const float*,
-                                      float*, float*, float*, float*);
+                                      float*, float*, float*, float*, bool);
 template crk_status rates_impl<double>(Plan*, cudaStream_t, char*, const double*, const double*,
-                                       double*, double*, double*, double*);
+                                       double*, double*, double*, double*, bool);
 
 }  // namespace crk

@@ -72,7 +72,7 @@ template <class R>
 crk_status moments_impl(Plan* plan, cudaStream_t st, char* ws, const R* m, R* V_out, R* coef_out);
 template <class R>
 crk_status rates_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u, R* dvdt,
-                      R* dudt, R* rho_out, R* gradv_out);
+                      R* dudt, R* rho_out, R* gradv_out, bool do_c2 = true);
 template <class R>
 crk_status moments_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* m,
                                const uint8_t* flags, R* V_state, R* coef_state);
@@ -91,7 +91,7 @@ crk_status forward_state_impl(Plan* plan, cudaStream_t st, char* ws, const R* v,
 template <class R>
 crk_status adjoint_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R* u,
                         const R* g_dvdt, const R* g_dudt, R* g_x, R* g_v, R* g_u, R* g_h,
-                        int recompute);
+                        int recompute, R* dvdt = nullptr, R* dudt = nullptr);
 
 // persistent grid size for a sweep kernel
 int sweep_grid(const Plan* plan, const void* kernel, int block, int smem);

@@ -158,6 +158,24 @@ class Solver:
                 "crk_adjoint")
         return gx, gv, gu, gh
 
+    def rates_adjoint(self, v, u, g_dvdt, g_dudt, out=None):
+        """Rates and their VJP for cotangents known in advance, in one pass
+        structure (the adjoint's pair sweep also accumulates the rates)."""
+        n = self.n
+        if out is None:
+            out = (torch.empty((3, n), dtype=self.dtype, device=self.device),
+                   torch.empty(n, dtype=self.dtype, device=self.device),
+                   torch.empty((3, n), dtype=self.dtype, device=self.device),
+                   torch.empty((3, n), dtype=self.dtype, device=self.device),
+                   torch.empty(n, dtype=self.dtype, device=self.device),
+                   torch.empty(n, dtype=self.dtype, device=self.device))
+        dvdt, dudt, gx, gv, gu, gh = out
+        L.check(L.crk_rates_adjoint(self.plan, _stream(), self._wsp, v.data_ptr(), u.data_ptr(),
+                                    g_dvdt.data_ptr(), g_dudt.data_ptr(), dvdt.data_ptr(),
+                                    dudt.data_ptr(), gx.data_ptr(), gv.data_ptr(), gu.data_ptr(),
+                                    gh.data_ptr()), "crk_rates_adjoint")
+        return out
+
     # -- gas and wind ----------------------------------------------------------------
     def set_species(self, species):
         """Species of the last build's particles (uint8, 0 gas, nonzero wind);

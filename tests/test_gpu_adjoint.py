@@ -221,3 +221,29 @@ def test_autotune_choices_keep_results(precision):
     assert rel(du1.double().cpu().numpy(), du0) < tol
     for a, b in zip(g1, g0):
         assert rel(a.double().cpu().numpy(), b) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fused_rates_adjoint_matches_separate_calls(precision):
+    """crk_rates_adjoint (the adjoint's pair sweep also forms the rates) gives
+    the rates of crk_rates and the gradients of crk_adjoint, to rounding."""
+    d = _box(seed=29)
+    n = d["h"].shape[0]
+    ga, gu = synth.cotangents(n, seed=12)
+    grads, (dv0, du0), s = _gpu_adjoint(d, precision, ga, gu)
+    t = to_dev(d, precision)
+    dt = t["h"].dtype
+    s.cell_build(t["x"], t["h"])
+    s.moments(t["m"])
+    out = s.rates_adjoint(t["v"], t["u"], torch.tensor(ga, dtype=dt, device="cuda"),
+                          torch.tensor(gu, dtype=dt, device="cuda"))
+    torch.cuda.synchronize()
+    assert s.poll() == 0
+    tol = 1e-13 if precision == "fp64" else 1e-6
+
+    def rel(a, b):
+        return np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(out[0].double().cpu().numpy(), dv0) < tol
+    assert rel(out[1].double().cpu().numpy(), du0) < tol
+    for a, b in zip(out[2:], grads):
+        assert rel(a.double().cpu().numpy(), b) < tol
