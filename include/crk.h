@@ -417,6 +417,19 @@ typedef struct {
 crk_status crk_timing_enable(crk_plan* plan, int32_t enable);
 crk_status crk_timing_read(crk_plan* plan, crk_kernel_time* out, int32_t cap, int32_t* count);
 
+/* Measured arithmetic peak of the current device: a grid of 8 blocks of 256
+ * threads per SM, each thread running 8 independent chains of fused
+ * multiply-adds (2 flops each) in float (fp64 = 0) or double (fp64 = 1), `iters`
+ * rounds of 16 per chain.  One warm-up launch, then three timed launches on
+ * `stream` (CUDA events); *flops_per_s receives the best rate and *ms
+ * (optional, host) that launch's duration.  The pair sweeps are bound by the
+ * FP32 pipes: this is the measured counterpart of their derived FP32 peak
+ * (SMs x 128 lanes x 2 flops x clock).  Allocates and frees a small device
+ * buffer and synchronises `stream`; not capturable.  CRK_EINVAL for iters <= 0
+ * or fp64 outside {0, 1}. */
+crk_status crk_alu_peak(crk_stream_t stream, int32_t fp64, int32_t iters, double* flops_per_s,
+                        double* ms);
+
 /* Gas volume V_i = m_i / sum_j m_j W(|x_ij|, h_i) of one periodic box without a
  * workspace.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- for example a subgrid operator

@@ -72,6 +72,8 @@ _SIGS = {
     "crk_status_string": (C.c_char_p, [C.c_int]),
     "crk_timing_enable": (C.c_int, [_VP, C.c_int32]),
     "crk_timing_read": (C.c_int, [_VP, _VP, C.c_int32, C.POINTER(C.c_int32)]),
+    "crk_alu_peak": (C.c_int, [_VP, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                               C.POINTER(C.c_double)]),
     "crk_autotune": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int32, _VP, _VP]),
     "crk_volume_static": (C.c_int, [_VP, C.c_int32, C.c_int64, C.c_double, C.c_double, _VP, _VP,
                                     _VP, _VP]),
@@ -217,6 +219,14 @@ def crk_timing_read(plan) -> list[tuple[str, float]]:
     cnt = C.c_int32()
     check(load().crk_timing_read(_VP(plan), buf, 256, C.byref(cnt)), "crk_timing_read")
     return [(buf[k].name.decode(), float(buf[k].ms)) for k in range(cnt.value)]
+
+
+def crk_alu_peak(stream, fp64: bool, iters: int) -> tuple[float, float]:
+    """(flops/s, ms) of the FMA-chain microbenchmark in float or double."""
+    f, ms = C.c_double(), C.c_double()
+    check(load().crk_alu_peak(_VP(stream), 1 if fp64 else 0, int(iters), C.byref(f), C.byref(ms)),
+          "crk_alu_peak")
+    return float(f.value), float(ms.value)
 
 
 def crk_volume_static(stream, precision, n, L, h_bound, x, h, m, V_out) -> int:
