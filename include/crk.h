@@ -358,9 +358,11 @@ crk_status crk_cool_exact(crk_plan* plan, crk_stream_t stream, int64_t n,
 /* Autotuner for the launch shapes of the eight neighbor sweeps (volume,
  * moments, density, rates and the four adjoint sweeps).  Each sweep is
  * compiled in CRK_TUNE_VARIANTS variants: three minimum numbers of resident
- * blocks per SM (so three register caps and occupancies), each with the
- * neighbor records read straight from global memory (variants 0-2) or copied
- * ahead through a per-thread shared-memory ring with cp.async (variants 3-5).
+ * blocks per SM (so three register caps and occupancies; variant % 3), each
+ * with the neighbor records read straight from global memory when the pair is
+ * evaluated (variants 0-2), copied ahead through a per-thread shared-memory
+ * ring with cp.async (variants 3-5), or loaded one list entry ahead into a
+ * register double buffer (variants 6-8).
  * This call runs crk_moments, crk_rates and, when g_dvdt and g_dudt are given,
  * crk_adjoint on the caller's data with each variant `repeats` times, times
  * every sweep with CUDA events and keeps the fastest variant per sweep in the
@@ -369,10 +371,16 @@ crk_status crk_cool_exact(crk_plan* plan, crk_stream_t stream, int64_t n,
  * choice_out (optional, host int32[8]) receives the chosen variant per sweep,
  * ms_out (optional, host float[8][CRK_TUNE_VARIANTS]) the mean milliseconds of
  * every variant.  Synchronises.  Requires a built workspace. */
-#define CRK_TUNE_VARIANTS 6
+#define CRK_TUNE_VARIANTS 9
 crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
                         const void* v, const void* u, const void* g_dvdt, const void* g_dudt,
                         int32_t repeats, int32_t* choice_out, float* ms_out);
+
+/* Set the launch variant of each of the eight sweeps (host int32[8], in the
+ * order of crk_autotune's choice_out, each in [0, CRK_TUNE_VARIANTS)) without
+ * timing anything: to replay a stored autotuner choice or to test a variant.
+ * Host only; CRK_EINVAL on a value out of range (nothing is changed then). */
+crk_status crk_tune_set(crk_plan* plan, const int32_t* choice);
 
 /* Test/inspection: the neighbor sets of the last build as CSR in caller order.
  * mode 0: gather set G(i) without the particle itself; mode 1: union set U(i).

@@ -75,6 +75,7 @@ _SIGS = {
     "crk_alu_peak": (C.c_int, [_VP, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                C.POINTER(C.c_double)]),
     "crk_autotune": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int32, _VP, _VP]),
+    "crk_tune_set": (C.c_int, [_VP, _VP]),
     "crk_volume_static": (C.c_int, [_VP, C.c_int32, C.c_int64, C.c_double, C.c_double, _VP, _VP,
                                     _VP, _VP]),
     "crk_cool_exact": (C.c_int, [_VP, _VP, C.c_int64, C.POINTER(crk_cool_table), C.c_double, _VP,
@@ -99,7 +100,7 @@ _SIGS = {
                             _VP, _VP, _VP, _VP, C.c_double, _VP, _VP, _VP]),
 }
 CRK_STATIC_MAX_PARTICLES = 65536
-CRK_TUNE_VARIANTS = 6  # launch variants per sweep (include/crk.h)
+CRK_TUNE_VARIANTS = 9  # launch variants per sweep (include/crk.h)
 
 _lib = None
 
@@ -313,6 +314,12 @@ def crk_rates_active(plan, stream, ws, v, u, rho_state, gradv_state, dvdt, dudt)
 
 SWEEPS = ("b1_volume", "b2_moments", "c1_density", "c2_rates", "adj_c2", "adj_c1", "adj_b2",
           "adj_b1")
+
+
+def crk_tune_set(plan, choice) -> None:
+    """Set the launch variant of every sweep (8 ints in the order of SWEEPS)."""
+    arr = (C.c_int32 * 8)(*[int(c) for c in choice])
+    check(load().crk_tune_set(_VP(plan), arr), "crk_tune_set")
 
 
 def crk_autotune(plan, stream, ws, m, v, u, g_dvdt, g_dudt, repeats=3):

@@ -476,6 +476,15 @@ crk_status crk_rates_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, cons
   return s;
 }
 
+crk_status crk_tune_set(crk_plan* plan, const int32_t* choice) {
+  if (!plan || !choice) return CRK_EINVAL;
+  for (int q = 0; q < 8; ++q)
+    if (choice[q] < 0 || choice[q] >= CRK_TUNE_VARIANTS) return CRK_EINVAL;
+  static const int queues[8] = {Q_B1, Q_B2, Q_C1, Q_C2, Q_A_C2, Q_A_C1, Q_A_B2, Q_A_B1};
+  for (int q = 0; q < 8; ++q) plan->impl.variant[queues[q]] = choice[q];
+  return CRK_OK;
+}
+
 crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
                         const void* v, const void* u, const void* g_dvdt, const void* g_dudt,
                         int32_t repeats, int32_t* choice_out, float* ms_out) {

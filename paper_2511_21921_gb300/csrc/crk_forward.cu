@@ -353,7 +353,7 @@ template <class R> struct PassC1 {
 template <class R> struct PassC2 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 128;
-  static constexpr int MB0 = 2, MB1 = 4, MB2 = 5;  // resident-block variants
+  static constexpr int MB0 = 2, MB1 = 3, MB2 = 4;  // resident-block variants
   static constexpr int QUEUE = Q_C2;
   using Real = R;
   static constexpr int SW0 = Rec<R>::C2, SW1 = 0;  // words staged per neighbor

@@ -34,7 +34,7 @@ struct Plan {
   int64_t n = 0;
   int32_t nb = 0;
   Tuning tune[16];
-  int variant[16] = {};  // launch variant per sweep: v % 3 -> MB0..MB2, v >= 3 staged ring
+  int variant[16] = {};  // launch variant per sweep: v % 3 -> MB0..MB2, v / 3 -> load mode
   // instrumentation
   long long launches = 0;
   bool timing = false;

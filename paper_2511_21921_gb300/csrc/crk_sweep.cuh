@@ -124,12 +124,15 @@ __device__ __forceinline__ void prefetch_sources(const typename P::Args& a, uint
 }
 
 // Persistent sweep: warps pull 32-particle work items from an atomic queue.
-// MINB (minimum resident blocks per SM) sets the register cap and STG routes
-// the neighbor records through the shared-memory ring; each pass is compiled
-// for three MINB values with and without the ring and the autotuner picks one
-// of the six per plan.
-template <class P, int MINB, bool STG>
+// MINB (minimum resident blocks per SM) sets the register cap and MODE how the
+// neighbor records reach the pair arithmetic: 0 loaded from global memory
+// when the pair is evaluated, 1 copied ahead through the shared-memory ring,
+// 2 loaded one entry ahead into a register double buffer.  Each pass is
+// compiled for three MINB values in each mode and the autotuner picks one of
+// the nine per plan.
+template <class P, int MINB, int MODE>
 __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args a) {
+  constexpr bool STG = MODE == 1;
   const int lane = threadIdx.x & 31;
   int32_t* q = &a.c.hdr->queue[P::QUEUE];
   extern __shared__ float4 ring[];
@@ -187,6 +190,35 @@ __global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args
         }
       }
       cp_async_wait<0>();
+    } else if constexpr (MODE == 2) {
+      // the gather part (gather passes) or the union list, with a register
+      // double buffer: the record of entry k+1 is loaded while the pair of
+      // entry k is evaluated, and the list entry one further ahead.  Unrolled
+      // by two so that the buffers alternate without register copies.
+      const int tot = lg + ls;
+      const int wmax = P::GATHER && !a.c.items ? a.c.wlen_g[w] : __reduce_max_sync(kFull, tot);
+      auto raw = [&](int k) -> uint32_t {
+        if (k >= tot) return 0u;
+        const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
+        return __ldg(col + slot * 32);
+      };
+      uint32_t enext = raw(0);
+      auto fetch = [&](int k, uint32_t& e, bool& ok, Real* r0, Real* r1) {
+        e = enext;
+        enext = raw(k + 1);
+        ok = k < tot && index_ok(a.c.hdr, e & kIdxMask, a.c.n);
+        if (ok) load_sources<P>(a, e & kIdxMask, r0, r1);
+      };
+      Real A0[P::SW0], A1[P::SW1 > 0 ? P::SW1 : 1], B0[P::SW0], B1[P::SW1 > 0 ? P::SW1 : 1];
+      uint32_t ea = 0u, eb = 0u;
+      bool oka = false, okb = false;
+      fetch(0, ea, oka, A0, A1);
+      for (int k = 0; k < wmax; k += 2) {
+        fetch(k + 1, eb, okb, B0, B1);
+        if (oka) P::pair_s(a, st, A0, A1, ea & kIdxMask, ea);
+        fetch(k + 2, ea, oka, A0, A1);
+        if (okb) P::pair_s(a, st, B0, B1, eb & kIdxMask, eb);
+      }
     } else if (P::GATHER) {
       // gather part only: the same row of every lane is one 128-byte line
       const int wg = a.c.items ? __reduce_max_sync(kFull, lg) : a.c.wlen_g[w];
@@ -448,29 +480,33 @@ template <class R> struct PairC2 {
   }
 };
 
-template <class P, int MB, bool STG>
+template <class P, int MB, int MODE>
 void launch_variant(Plan* plan, cudaStream_t st, const typename P::Args& a) {
-  const size_t smem = STG ? Stage<P>::bytes : 0;
-  const void* fn = (const void*)k_sweep<P, MB, STG>;
+  const size_t smem = MODE == 1 ? Stage<P>::bytes : 0;
+  const void* fn = (const void*)k_sweep<P, MB, MODE>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int grid = sweep_grid(plan, fn, P::BLOCK, (int)smem);
-  k_sweep<P, MB, STG><<<grid, P::BLOCK, smem, st>>>(a);
+  k_sweep<P, MB, MODE><<<grid, P::BLOCK, smem, st>>>(a);
 }
 
 // Variant v of a sweep: v % 3 picks the resident-block count (MB0..MB2),
-// v >= 3 the shared-memory ring.
+// v / 3 the mode (0 plain loads, 1 shared-memory ring, 2 register double
+// buffer).
 template <class P>
 void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const char* name) {
   const int v = plan->variant[P::QUEUE];
   Phase ph(plan, st, name, 1);
   switch (v) {
-    case 1: launch_variant<P, P::MB1, false>(plan, st, a); break;
-    case 2: launch_variant<P, P::MB2, false>(plan, st, a); break;
-    case 3: launch_variant<P, P::MB0, true>(plan, st, a); break;
-    case 4: launch_variant<P, P::MB1, true>(plan, st, a); break;
-    case 5: launch_variant<P, P::MB2, true>(plan, st, a); break;
-    default: launch_variant<P, P::MB0, false>(plan, st, a); break;
+    case 1: launch_variant<P, P::MB1, 0>(plan, st, a); break;
+    case 2: launch_variant<P, P::MB2, 0>(plan, st, a); break;
+    case 3: launch_variant<P, P::MB0, 1>(plan, st, a); break;
+    case 4: launch_variant<P, P::MB1, 1>(plan, st, a); break;
+    case 5: launch_variant<P, P::MB2, 1>(plan, st, a); break;
+    case 6: launch_variant<P, P::MB0, 2>(plan, st, a); break;
+    case 7: launch_variant<P, P::MB1, 2>(plan, st, a); break;
+    case 8: launch_variant<P, P::MB2, 2>(plan, st, a); break;
+    default: launch_variant<P, P::MB0, 0>(plan, st, a); break;
   }
 }
 

@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import oracle
+from paper_2511_21921_gb300 import _lib as L
 from paper_2511_21921_gb300 import synth
 from paper_2511_21921_gb300.solver import Solver, rates
 
@@ -209,7 +210,8 @@ def test_autotune_choices_keep_results(precision):
     tuned = s.autotune(t["m"], t["v"], t["u"], gat, gut, repeats=2)
     assert set(tuned) == {"b1_volume", "b2_moments", "c1_density", "c2_rates", "adj_c2",
                           "adj_c1", "adj_b2", "adj_b1"}
-    assert all(v["variant"] in range(6) and min(v["ms"]) > 0 for v in tuned.values())
+    assert all(v["variant"] in range(L.CRK_TUNE_VARIANTS) and min(v["ms"]) > 0
+               for v in tuned.values())
     dv1, du1, _, _ = s.rates(t["v"], t["u"])
     g1 = s.adjoint(t["v"], t["u"], gat, gut, recompute=False)
     torch.cuda.synchronize()
