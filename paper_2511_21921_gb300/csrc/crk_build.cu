@@ -623,27 +623,29 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
         if (act) {
           if (fast) {
             // float predicate on the nearest images: no per-pair wrap.  All
-            // 32 staged candidates are tested branch-free into two bit
-            // masks; only the hits (a few per stage) are then emitted, in
-            // candidate order.
+            // 32 staged candidates are tested branch-free into one bit mask
+            // of the union predicate r^2 < max(h_i^2, h_j^2); only the hits
+            // (a few per stage) are then emitted, in candidate order, with
+            // the same r^2 recomputed to tell gather from scatter-only.
             const float hi2f = (float)hi * (float)hi;
-            uint32_t mg = 0u, msc = 0u;
+            uint32_t hit = 0u;
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
               const float4 t = s4[wib][k];
               const float dx = p[0] - t.x, dy = p[1] - t.y, dz = p[2] - t.z;
               const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-              mg |= (r2 < hi2f ? 1u : 0u) << k;
-              msc |= (r2 < t.w ? 1u : 0u) << k;
+              hit |= (r2 < fmaxf(hi2f, t.w) ? 1u : 0u) << k;
             }
-            uint32_t hit = mg | msc;
             while (hit) {
               const int k = __ffs(hit) - 1;
               hit &= hit - 1u;
               const int32_t j = sj[wib][k];
               if (j == s) continue;
-              const bool g = (mg >> k) & 1u;
-              const bool sc = (msc >> k) & 1u;
+              const float4 t = s4[wib][k];
+              const float dx = p[0] - t.x, dy = p[1] - t.y, dz = p[2] - t.z;
+              const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+              const bool g = r2 < hi2f;
+              const bool sc = r2 < t.w;
               const uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
               if (kg + ks < cap_pp) {
                 const int64_t kk = g ? kg : cap_pp - 1 - ks;

@@ -14,7 +14,7 @@ namespace crk {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarp = 32;
 constexpr int kBucket = 8;          // particles per tree leaf (bucket)
-constexpr int kSortTile = 4096;     // keys per radix-sort tile
+constexpr int kSortTile = 1024;     // keys per radix-sort tile (small: enough blocks to fill the GPU)
 constexpr int kSortThreads = 256;
 constexpr int kStackDepth = 96;     // tree traversal stack (depth <= 64 key bits + 30 index bits)
 constexpr uint32_t kIdxMask = 0x3fffffffu;
