@@ -354,6 +354,15 @@ __global__ void k_lbvh(const uint64_t* __restrict__ keys, int64_t nbk, int64_t n
   if (i == 0) parent[0] = -1;
 }
 
+// Arrival count at a node with acquire-release ordering at device scope: the
+// releasing add publishes this thread's earlier writes (the child's bounds),
+// and the acquiring add of the second arrival makes them visible to it.
+__device__ __forceinline__ int arrive_acq_rel(int32_t* p) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+  return old;
+}
+
 // bottom-up bounds: the second child to arrive at a node merges both.
 __global__ void k_refit(int64_t nbk, int64_t ni, int64_t nt, const int32_t* __restrict__ child,
                         const int32_t* __restrict__ parent, int32_t* __restrict__ visit,
@@ -362,9 +371,7 @@ __global__ void k_refit(int64_t nbk, int64_t ni, int64_t nt, const int32_t* __re
   if (b >= nbk) return;
   int32_t node = parent[ni + b];
   while (node >= 0) {
-    __threadfence();
-    if (atomicAdd(&visit[node], 1) == 0) return;
-    __threadfence();
+    if (arrive_acq_rel(&visit[node]) == 0) return;
     int32_t c0 = child[2 * node], c1 = child[2 * node + 1];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
