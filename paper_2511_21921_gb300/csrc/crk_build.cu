@@ -557,19 +557,32 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
         cnt_nodes += take;
         __syncwarp();
         bool ov = false;
-        if (node >= 0 && b >= brange[node] && b <= brange[nt + node]) {
-          float R_ = fmaxf(hg, hmaxn[node]) * 1.00001f + 1e-6f * Lf;
-          float g2 = 0.f;
+        int2 ch = make_int2(0, 0);
+        if (node >= 0) {
+          // every field of the node (and its children) is requested at once,
+          // so the box-range test costs no extra round trip to memory
+          const int32_t b0 = __ldg(brange + node), b1 = __ldg(brange + nt + node);
+          const float hm = __ldg(hmaxn + node);
+          float lo[3], hi_[3];
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
-            const float lo = aabb[a * nt + node], hi_ = aabb[(3 + a) * nt + node];
-            float dd = gc[a] - 0.5f * (lo + hi_);
-            if (dd > halfLf) dd -= Lf;
-            else if (dd < -halfLf) dd += Lf;
-            dd = fabsf(dd) - ge[a] - 0.5f * (hi_ - lo);
-            if (dd > 0.f) g2 += dd * dd;
+            lo[a] = __ldg(aabb + a * nt + node);
+            hi_[a] = __ldg(aabb + (3 + a) * nt + node);
           }
-          ov = g2 <= R_ * R_;
+          if (node < ni) ch = __ldg(reinterpret_cast<const int2*>(child) + node);
+          if (b >= b0 && b <= b1) {
+            const float R_ = fmaxf(hg, hm) * 1.00001f + 1e-6f * Lf;
+            float g2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              float dd = gc[a] - 0.5f * (lo[a] + hi_[a]);
+              if (dd > halfLf) dd -= Lf;
+              else if (dd < -halfLf) dd += Lf;
+              dd = fabsf(dd) - ge[a] - 0.5f * (hi_[a] - lo[a]);
+              if (dd > 0.f) g2 += dd * dd;
+            }
+            ov = g2 <= R_ * R_;
+          }
         }
         const bool leaf = node >= ni;
         const unsigned ml = __ballot_sync(kFull, ov && leaf);
@@ -583,8 +596,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
         }
         if (ov && !leaf) {
           const int at = sp + 2 * __popc(mi & lt);
-          stk[wib][at] = child[2 * node];
-          stk[wib][at + 1] = child[2 * node + 1];
+          stk[wib][at] = ch.x;
+          stk[wib][at + 1] = ch.y;
         }
         sp += npush;
         __syncwarp();
@@ -597,28 +610,40 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
         {
           const int kb = lane >> 3;
           int64_t j = -1;
-          if (kb < take) {
-            const int64_t jj = (int64_t)cand[wib][nc + kb] * kBucket + (lane & 7);
-            if (jj < n && boxid[jj] == b) j = jj;
-          }
-          sj[wib][lane] = (int32_t)j;
           if (fast) {
             // float position moved to the periodic image nearest the group
-            // center; NaN for slots that hold no particle of this box
+            // center; NaN for slots that hold no particle of this box.  The
+            // position is requested together with the box id.
             float4 t = make_float4(__int_as_float(0x7fffffff), 0.f, 0.f, __int_as_float(0x7fffffff));
-            if (j >= 0) {
-              float q[3];
+            if (kb < take) {
+              const int64_t jj = (int64_t)cand[wib][nc + kb] * kBucket + (lane & 7);
+              if (jj < n) {
+                const int32_t bj = __ldg(boxid + jj);
+                float q[3];
 #pragma unroll
-              for (int a = 0; a < 3; ++a) {
-                q[a] = (float)xs[a * n + j];
-                const float dd = gc[a] - q[a];
-                q[a] += dd > halfLf ? Lf : (dd < -halfLf ? -Lf : 0.f);
+                for (int a = 0; a < 3; ++a) q[a] = (float)__ldg(xs + a * n + jj);
+                const float hj = (float)__ldg(hs + jj);
+                if (bj == b) {
+                  j = jj;
+#pragma unroll
+                  for (int a = 0; a < 3; ++a) {
+                    const float dd = gc[a] - q[a];
+                    q[a] += dd > halfLf ? Lf : (dd < -halfLf ? -Lf : 0.f);
+                  }
+                  t = make_float4(q[0], q[1], q[2], hj * hj);
+                }
               }
-              const float hj = (float)hs[j];
-              t = make_float4(q[0], q[1], q[2], hj * hj);
             }
+            sj[wib][lane] = (int32_t)j;
             s4[wib][lane] = t;
-          } else if (j >= 0) {
+          } else {
+            if (kb < take) {
+              const int64_t jj = (int64_t)cand[wib][nc + kb] * kBucket + (lane & 7);
+              if (jj < n && boxid[jj] == b) j = jj;
+            }
+            sj[wib][lane] = (int32_t)j;
+          }
+          if (!fast && j >= 0) {
             R t[XW];
             load_x(xs, n, j, t);
 #pragma unroll
