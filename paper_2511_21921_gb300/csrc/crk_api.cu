@@ -59,6 +59,8 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.child = take(4 * 2 * NI);
   L.parent = take(4 * NT);
   L.visit = take(4 * NI);
+  L.p4 = take(16 * N);
+  L.nrec = take(4 * kNodeRec * NT);
   L.cnt_g = take(4 * N);
   L.cnt_s = take(4 * N);
   L.wlen_g = take(4 * NW);

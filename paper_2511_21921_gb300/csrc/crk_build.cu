@@ -264,7 +264,7 @@ template <class R>
 __global__ void k_gather_sorted(const uint64_t* __restrict__ keys, const int32_t* __restrict__ idx,
                                 const double* __restrict__ x, const R* __restrict__ h, int64_t n,
                                 int32_t* __restrict__ perm, int32_t* __restrict__ boxid,
-                                R* __restrict__ xs, R* __restrict__ hs) {
+                                R* __restrict__ xs, R* __restrict__ hs, float4* __restrict__ p4) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   int32_t p = idx[s];
@@ -272,7 +272,12 @@ __global__ void k_gather_sorted(const uint64_t* __restrict__ keys, const int32_t
   boxid[s] = (int32_t)(keys[s] >> 48);
   double xd[3] = {x[p], x[n + p], x[2 * n + p]};
   put_x(xs, n, s, xd);
-  hs[s] = h[p];
+  const R hp = h[p];
+  hs[s] = hp;
+  // float position (round to nearest, the high part of the split position)
+  // and h for the list build's float candidate test
+  p4[s] = make_float4(__double2float_rn(xd[0]), __double2float_rn(xd[1]),
+                      __double2float_rn(xd[2]), (float)hp);
 }
 
 // ---------------------------------------------------------------------------
@@ -386,6 +391,37 @@ __global__ void k_refit(int64_t nbk, int64_t ni, int64_t nt, const int32_t* __re
   }
 }
 
+// Packed node records for the list build: lo[3], hi[3], h_max, then the box
+// range and the two children as integers, so that a node test is two 32-byte
+// loads instead of ten scattered ones.
+__global__ void k_pack_nodes(int64_t nt, int64_t ni, const float* __restrict__ aabb,
+                             const float* __restrict__ hmaxn, const int32_t* __restrict__ brange,
+                             const int32_t* __restrict__ child, float* __restrict__ nrec) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nt) return;
+  float r[kNodeRec];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) r[a] = aabb[a * nt + k];
+  r[6] = hmaxn[k];
+  r[7] = __int_as_float(brange[k]);
+  r[8] = __int_as_float(brange[nt + k]);
+  r[9] = __int_as_float(k < ni ? child[2 * k] : -1);
+  r[10] = __int_as_float(k < ni ? child[2 * k + 1] : -1);
+#pragma unroll
+  for (int a = 11; a < kNodeRec; ++a) r[a] = 0.f;
+  float4* o = reinterpret_cast<float4*>(nrec + k * kNodeRec);
+#pragma unroll
+  for (int v = 0; v < kNodeRec / 4; ++v) o[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+}
+
+// 32-byte read-only load (one 256-bit access)
+__device__ __forceinline__ void ld8(const float* p, float* o) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]),
+        "=f"(o[7])
+      : "l"(p));
+}
+
 // ---------------------------------------------------------------------------
 // neighbor lists: one thread per sorted particle traverses the tree
 // ---------------------------------------------------------------------------
@@ -453,9 +489,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
     const uint64_t* __restrict__ keys, const R* __restrict__ xs, const R* __restrict__ hs,
     const int32_t* __restrict__ boxid,
     const double* __restrict__ box_L, int64_t n, int64_t nbk, int64_t ni, int64_t nt,
-    const float* __restrict__ aabb, const float* __restrict__ hmaxn,
-    const int32_t* __restrict__ brange, const int32_t* __restrict__ child,
-    int32_t* __restrict__ cnt_g, int32_t* __restrict__ cnt_s, int32_t* __restrict__ wlen_g,
+    const float* __restrict__ nrec, const float4* __restrict__ p4, int32_t* __restrict__ cnt_g, int32_t* __restrict__ cnt_s, int32_t* __restrict__ wlen_g,
     int32_t* __restrict__ wlen_s, uint32_t* __restrict__ ell, int64_t cap_pp, DevHeader* hdr) {
   constexpr int XW = Prec<R>::XW;
   __shared__ int32_t stk[kNbrWarps][kNodeStack];
@@ -520,7 +554,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
     group_bounds(act, p, (float)hi, gc, ge, hg);
     // nearest-image staging is exact for every pair in reach when the group
     // extent plus the largest search radius stays below half the box
-    const float reach = fmaxf(hg, hmaxn[0]);
+    const float reach = fmaxf(hg, __ldg(nrec + 6));  // h_max of the root
     const bool fast = sizeof(R) == 4 &&
                       2.f * fmaxf(ge[0], fmaxf(ge[1], ge[2])) + reach < 0.49f * Lf;
     if (__popc(m) > 2 && ntodo <= 6) {
@@ -559,17 +593,16 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
         bool ov = false;
         int2 ch = make_int2(0, 0);
         if (node >= 0) {
-          // every field of the node (and its children) is requested at once,
-          // so the box-range test costs no extra round trip to memory
-          const int32_t b0 = __ldg(brange + node), b1 = __ldg(brange + nt + node);
-          const float hm = __ldg(hmaxn + node);
-          float lo[3], hi_[3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            lo[a] = __ldg(aabb + a * nt + node);
-            hi_[a] = __ldg(aabb + (3 + a) * nt + node);
-          }
-          if (node < ni) ch = __ldg(reinterpret_cast<const int2*>(child) + node);
+          // the whole node record (bounds, h_max, box range, children) in
+          // two 256-bit loads
+          float nr[16];
+          ld8(nrec + (int64_t)node * kNodeRec, nr);
+          ld8(nrec + (int64_t)node * kNodeRec + 8, nr + 8);
+          const int32_t b0 = __float_as_int(nr[7]), b1 = __float_as_int(nr[8]);
+          const float hm = nr[6];
+          const float* lo = nr;
+          const float* hi_ = nr + 3;
+          ch = make_int2(__float_as_int(nr[9]), __float_as_int(nr[10]));
           if (b >= b0 && b <= b1) {
             const float R_ = fmaxf(hg, hm) * 1.00001f + 1e-6f * Lf;
             float g2 = 0.f;
@@ -619,10 +652,9 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
               const int64_t jj = (int64_t)cand[wib][nc + kb] * kBucket + (lane & 7);
               if (jj < n) {
                 const int32_t bj = __ldg(boxid + jj);
-                float q[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) q[a] = (float)__ldg(xs + a * n + jj);
-                const float hj = (float)__ldg(hs + jj);
+                const float4 pj = __ldg(p4 + jj);
+                float q[3] = {pj.x, pj.y, pj.z};
+                const float hj = pj.w;
                 if (bj == b) {
                   j = jj;
 #pragma unroll
@@ -822,8 +854,10 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   R* xs = reinterpret_cast<R*>(ws + Ly.xs);
   R* hs = reinterpret_cast<R*>(ws + Ly.hs);
   ph_sort.end();
-  Phase ph_tree(plan, st, "build.tree", Ly.ni > 0 ? 4 : 2);
-  k_gather_sorted<R><<<g256, 256, 0, st>>>(k0, v0, x, h, n, perm, boxid, xs, hs);
+  Phase ph_tree(plan, st, "build.tree", Ly.ni > 0 ? 5 : 3);
+  float4* p4 = reinterpret_cast<float4*>(ws + Ly.p4);
+  float* nrec = reinterpret_cast<float*>(ws + Ly.nrec);
+  k_gather_sorted<R><<<g256, 256, 0, st>>>(k0, v0, x, h, n, perm, boxid, xs, hs, p4);
   // bucket tree
   float* aabb = reinterpret_cast<float*>(ws + Ly.aabb);
   float* hmaxn = reinterpret_cast<float*>(ws + Ly.hmaxn);
@@ -840,6 +874,8 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
     k_refit<<<(unsigned)((nbk + 255) / 256), 256, 0, st>>>(nbk, ni, nt, child, parent, visit, aabb,
                                                           hmaxn, brange);
   }
+  k_pack_nodes<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, ni, aabb, hmaxn, brange, child,
+                                                            nrec);
   ph_tree.end();
   Phase ph_lists(plan, st, "build.lists", 1);
   // neighbor lists (one pass; fixed column of cap_pp slots per particle)
@@ -849,9 +885,8 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   int32_t* wlen_s = reinterpret_cast<int32_t*>(ws + Ly.wlen_s);
   uint32_t* ell = reinterpret_cast<uint32_t*>(ws + Ly.ell);
   const unsigned gw = (unsigned)((Ly.nw + kNbrWarps - 1) / kNbrWarps);
-  k_nbr<R><<<gw, kNbrWarps * 32, 0, st>>>(k0, xs, hs, boxid, wbox, n, nbk, ni, nt, aabb, hmaxn,
-                                          brange, child, cnt_g, cnt_s, wlen_g, wlen_s, ell,
-                                          Ly.cap_pp, hdr);
+  k_nbr<R><<<gw, kNbrWarps * 32, 0, st>>>(k0, xs, hs, boxid, wbox, n, nbk, ni, nt, nrec, p4,
+                                          cnt_g, cnt_s, wlen_g, wlen_s, ell, Ly.cap_pp, hdr);
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }
 

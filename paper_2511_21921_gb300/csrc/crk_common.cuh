@@ -16,6 +16,7 @@ constexpr int kWarp = 32;
 constexpr int kBucket = 8;          // particles per tree leaf (bucket)
 constexpr int kSortTile = 1024;     // keys per radix-sort tile (small: enough blocks to fill the GPU)
 constexpr int kSortThreads = 256;
+constexpr int kNodeRec = 16;        // words per packed tree-node record (64 bytes)
 constexpr int kStackDepth = 96;     // tree traversal stack (depth <= 64 key bits + 30 index bits)
 constexpr uint32_t kIdxMask = 0x3fffffffu;
 constexpr uint32_t kGatherBit = 0x80000000u;   // j in G(i):  r < h_i
@@ -271,6 +272,9 @@ struct Layout {
   size_t key0 = 0, key1 = 0, val0 = 0, val1 = 0, hist = 0, scan_tmp = 0;
   size_t perm = 0, boxid = 0, xs = 0, hs = 0, ms = 0, us = 0, vs = 0;
   size_t aabb = 0, hmaxn = 0, brange = 0, child = 0, parent = 0, visit = 0;
+  // the list build's packed copies: float4 (x, y, z, h) per sorted particle
+  // and one 64-byte record per tree node (bounds, h_max, box range, children)
+  size_t p4 = 0, nrec = 0;
   size_t cnt_g = 0, cnt_s = 0, wlen_g = 0, wlen_s = 0, ell = 0;
   size_t rec_b1 = 0, rec_b2 = 0, rec_c1 = 0, rec_c2 = 0, coef = 0, Vs = 0, rhos = 0;
   size_t gvs = 0, Ds = 0;
