@@ -163,6 +163,8 @@ __global__ void k_scan_apply(const T* __restrict__ in, int64_t n, const T* __res
   }
 }
 
+int scan_launches(int64_t n) { return n <= 0 ? 0 : 3; }
+
 size_t scan_tmp_bytes(int64_t n) {
   int64_t np = (n + kScanChunk - 1) / kScanChunk + 1;
   return (size_t)np * sizeof(int64_t) + 256;
@@ -836,7 +838,8 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   int box_bits = 0;
   while ((1ll << box_bits) < nb) ++box_bits;
   int passes = (48 + box_bits + 7) / 8;
-  Phase ph_sort(plan, st, "build.keys_sort", 1 + 5 * passes);
+  Phase ph_sort(plan, st, "build.keys_sort",
+                1 + passes * (2 + scan_launches((int64_t)256 * Ly.ntiles)));
   k_keys<R><<<g256, 256, 0, st>>>(x, h, box_off, box_L, nb, n, k0, v0, hdr);
   // radix sort over the used key bits
   uint32_t* hist = reinterpret_cast<uint32_t*>(ws + Ly.hist);

@@ -640,7 +640,7 @@ crk_status moments_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* m
   int32_t* items_a = reinterpret_cast<int32_t*>(ws + Ly.items_a);
   const unsigned g = (unsigned)((n + 255) / 256);
   {
-    Phase ph(plan, st, "active_lists", 5);
+    Phase ph(plan, st, "active_lists", 3 + 2 * scan_launches(n));
     k_active_flags<<<g, 256, 0, st>>>(flags, c.perm, n, flg, pr, pa);
     uint32_t* counts = reinterpret_cast<uint32_t*>(c.hdr->n_items);
     exclusive_scan<uint32_t>(pr, qr, n, ws + Ly.scan_tmp, counts, st);

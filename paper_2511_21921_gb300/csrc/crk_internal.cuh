@@ -60,6 +60,7 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb);
 
 template <class T>
 void exclusive_scan(const T* in, T* out, int64_t n, void* tmp, T* total_out, cudaStream_t st);
+int scan_launches(int64_t n);  // kernels exclusive_scan launches for n elements
 
 template <class R>
 crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int32_t nb,
