@@ -50,7 +50,7 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
 template <class R>
 __global__ void k_keys(const double* __restrict__ x, const R* __restrict__ h,
                        const int64_t* __restrict__ box_off, const double* __restrict__ box_L,
-                       int32_t nb, int64_t n, uint64_t* __restrict__ keys,
+                       int32_t nb, int64_t n, int bits, uint64_t* __restrict__ keys,
                        int32_t* __restrict__ vals, DevHeader* hdr) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -63,8 +63,9 @@ __global__ void k_keys(const double* __restrict__ x, const R* __restrict__ h,
     double xa = x[a * n + i];
     if (!isfinite(xa)) { set_status(hdr, CRK_ENONFINITE); ok = false; }
     else if (!(xa >= 0.0 && xa < L)) { set_status(hdr, CRK_EDOMAIN); ok = false; }
-    double t = ok ? floor(xa / L * 65536.0) : 0.0;
-    t = t < 0.0 ? 0.0 : (t > 65535.0 ? 65535.0 : t);
+    const double cells = (double)(1u << bits);
+    double t = ok ? floor(xa / L * cells) : 0.0;
+    t = t < 0.0 ? 0.0 : (t > cells - 1.0 ? cells - 1.0 : t);
     q[a] = (uint32_t)t;
   }
   double hi = (double)h[i];
@@ -837,17 +838,25 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   int32_t* v1 = reinterpret_cast<int32_t*>(ws + Ly.val1);
   int box_bits = 0;
   while ((1ll << box_bits) < nb) ++box_bits;
-  int passes = (48 + box_bits + 7) / 8;
+  // Morton resolution per axis: six bits finer than the mean spacing of the
+  // largest possible box (n particles), at most 16.  Finer keys only order
+  // particles that share a cell more finely; the lists do not depend on it.
+  int bits = 6;
+  while (bits < 16 && (double)(1ll << (3 * (bits - 6))) < (double)n) ++bits;
+  // 8-bit digits over the Morton bits [0, 3 bits) and the box bits [48, ...)
+  int shifts[8], passes = 0;
+  for (int b = 0; b < 3 * bits; b += 8) shifts[passes++] = b;
+  for (int b = 48; b < 48 + box_bits; b += 8) shifts[passes++] = b;
   Phase ph_sort(plan, st, "build.keys_sort",
                 1 + passes * (2 + scan_launches((int64_t)256 * Ly.ntiles)));
-  k_keys<R><<<g256, 256, 0, st>>>(x, h, box_off, box_L, nb, n, k0, v0, hdr);
+  k_keys<R><<<g256, 256, 0, st>>>(x, h, box_off, box_L, nb, n, bits, k0, v0, hdr);
   // radix sort over the used key bits
   uint32_t* hist = reinterpret_cast<uint32_t*>(ws + Ly.hist);
   int ntiles = (int)Ly.ntiles;
   for (int p = 0; p < passes; ++p) {
-    k_rsort_hist<<<ntiles, kSortThreads, 0, st>>>(k0, n, 8 * p, ntiles, hist);
+    k_rsort_hist<<<ntiles, kSortThreads, 0, st>>>(k0, n, shifts[p], ntiles, hist);
     exclusive_scan<uint32_t>(hist, hist, (int64_t)256 * ntiles, ws + Ly.scan_tmp, nullptr, st);
-    k_rsort_scatter<<<ntiles, kSortThreads, 0, st>>>(k0, v0, k1, v1, hist, n, 8 * p, ntiles);
+    k_rsort_scatter<<<ntiles, kSortThreads, 0, st>>>(k0, v0, k1, v1, hist, n, shifts[p], ntiles);
     std::swap(k0, k1);
     std::swap(v0, v1);
   }
