@@ -353,6 +353,7 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "fused_rates_adjoint": fused,
         "autotune": {k: v["variant"] for k, v in tuned.items()} if tuned else None,
+        "autotune_ms": {k: v["ms"] for k, v in tuned.items()} if tuned else None,
         "graph": bool(graph is not None),
         "eager_ms_per_step": round(sum(ms_eager) / len(ms_eager), 4),
         "fwd_pairs_per_s": pairs / (fwd_ms * 1e-3) if fwd_ms > 0 else None,

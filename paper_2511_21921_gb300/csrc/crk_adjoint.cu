@@ -222,7 +222,7 @@ __global__ void k_adj_prep(const R* __restrict__ gdv, const R* __restrict__ gdu,
 template <class R> struct PassA2 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
-  static constexpr int MB0 = 1, MB1 = 6, MB2 = 8;  // resident-block variants
+  static constexpr int MB0 = 1, MB1 = 5, MB2 = 6;  // resident-block variants
   static constexpr int QUEUE = Q_A_C2;
   using Real = R;
   static constexpr int SW0 = Rec<R>::C2, SW1 = 4;  // words staged per neighbor

@@ -130,8 +130,16 @@ __device__ __forceinline__ void prefetch_sources(const typename P::Args& a, uint
 // 2 loaded one entry ahead into a register double buffer.  Each pass is
 // compiled for three MINB values in each mode and the autotuner picks one of
 // the nine per plan.
+// Register cap that lets MINB blocks of `block` threads share an SM's 64 K
+// registers (a multiple of 8, at most 255).
+constexpr int sweep_regs(int block, int minb) {
+  const int r = (65536 / (minb * block)) & ~7;
+  return r > 255 ? 255 : r;
+}
+
 template <class P, int MINB, int MODE>
-__global__ void __launch_bounds__(P::BLOCK, MINB) k_sweep(const typename P::Args a) {
+__global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MINB))
+    k_sweep(const typename P::Args a) {
   constexpr bool STG = MODE == 1;
   const int lane = threadIdx.x & 31;
   int32_t* q = &a.c.hdr->queue[P::QUEUE];
