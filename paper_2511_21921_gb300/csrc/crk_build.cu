@@ -499,8 +499,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
   __shared__ int32_t cand[kNbrWarps][64];
   __shared__ R sx[kNbrWarps][XW][32];
   __shared__ R sh[kNbrWarps][32];
-  __shared__ float4 s4[kNbrWarps][32];
-  __shared__ int32_t sj[kNbrWarps][32];
+  __shared__ float4 s4[kNbrWarps][64];
+  __shared__ int32_t sj[kNbrWarps][64];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kNbrWarps + wib;
   const int64_t nw = (n + 31) / 32;
@@ -583,6 +583,40 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
       }
     }
     int sp = 0, nc = 0;
+    int ns = 0;  // candidates waiting in the stage (float path)
+    const float hi2f = (float)hi * (float)hi;
+    // float predicate on the nearest images: no per-pair wrap.  The 32
+    // staged candidates are tested branch-free into one bit mask of the union
+    // predicate r^2 < max(h_i^2, h_j^2); only the hits (a few per stage) are
+    // then emitted, in candidate order, with the same r^2 recomputed to tell
+    // gather from scatter-only.
+    auto test_stage = [&]() {
+      uint32_t hit = 0u;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float4 t = s4[wib][k];
+        const float dx = p[0] - t.x, dy = p[1] - t.y, dz = p[2] - t.z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        hit |= (r2 < fmaxf(hi2f, t.w) ? 1u : 0u) << k;
+      }
+      while (hit) {
+        const int k = __ffs(hit) - 1;
+        hit &= hit - 1u;
+        const int32_t j = sj[wib][k];
+        if (j == s) continue;
+        const float4 t = s4[wib][k];
+        const float dx = p[0] - t.x, dy = p[1] - t.y, dz = p[2] - t.z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const bool g = r2 < hi2f;
+        const bool sc = r2 < t.w;
+        const uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
+        if (kg + ks < cap_pp) {
+          const int64_t kk = g ? kg : cap_pp - 1 - ks;
+          ell[wbase + kk * 32] = e;
+        }
+        if (g) ++kg; else ++ks;
+      }
+    };
     if (lane == 0) stk[wib][0] = (ni > 0) ? 0 : (int32_t)ni;
     sp = 1;
     __syncwarp();
@@ -643,84 +677,75 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
         nc -= take;
         cnt_buckets += take;
         // stage the particles of buckets cand[nc .. nc+take)
-        {
-          const int kb = lane >> 3;
+        const int kb = lane >> 3;
+        if (fast) {
+          // float position moved to the periodic image nearest the group
+          // center (requested together with the box id).  A particle that
+          // lies farther from the group's box than max(h_group, h_j) cannot
+          // be a union neighbor of any lane and is dropped here; the others
+          // are appended to the stage, which is tested once it holds 32.
+          // Dropping preserves the order of the survivors, so every list
+          // comes out exactly as without the filter.
           int64_t j = -1;
-          if (fast) {
-            // float position moved to the periodic image nearest the group
-            // center; NaN for slots that hold no particle of this box.  The
-            // position is requested together with the box id.
-            float4 t = make_float4(__int_as_float(0x7fffffff), 0.f, 0.f, __int_as_float(0x7fffffff));
-            if (kb < take) {
-              const int64_t jj = (int64_t)cand[wib][nc + kb] * kBucket + (lane & 7);
-              if (jj < n) {
-                const int32_t bj = __ldg(boxid + jj);
-                const float4 pj = __ldg(p4 + jj);
-                float q[3] = {pj.x, pj.y, pj.z};
-                const float hj = pj.w;
-                if (bj == b) {
-                  j = jj;
+          float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+          bool pass = false;
+          if (kb < take) {
+            const int64_t jj = (int64_t)cand[wib][nc + kb] * kBucket + (lane & 7);
+            if (jj < n) {
+              const int32_t bj = __ldg(boxid + jj);
+              const float4 pj = __ldg(p4 + jj);
+              float q[3] = {pj.x, pj.y, pj.z};
+              const float hj = pj.w;
+              if (bj == b) {
+                j = jj;
+                float g2 = 0.f;
 #pragma unroll
-                  for (int a = 0; a < 3; ++a) {
-                    const float dd = gc[a] - q[a];
-                    q[a] += dd > halfLf ? Lf : (dd < -halfLf ? -Lf : 0.f);
-                  }
-                  t = make_float4(q[0], q[1], q[2], hj * hj);
+                for (int a = 0; a < 3; ++a) {
+                  const float dd = gc[a] - q[a];
+                  q[a] += dd > halfLf ? Lf : (dd < -halfLf ? -Lf : 0.f);
+                  const float o = fabsf(q[a] - gc[a]) - ge[a];
+                  if (o > 0.f) g2 += o * o;
                 }
+                const float Rj = fmaxf(hg, hj) * 1.00001f + 1e-6f * Lf;
+                pass = g2 <= Rj * Rj;
+                t = make_float4(q[0], q[1], q[2], hj * hj);
               }
             }
-            sj[wib][lane] = (int32_t)j;
-            s4[wib][lane] = t;
-          } else {
-            if (kb < take) {
-              const int64_t jj = (int64_t)cand[wib][nc + kb] * kBucket + (lane & 7);
-              if (jj < n && boxid[jj] == b) j = jj;
-            }
-            sj[wib][lane] = (int32_t)j;
           }
-          if (!fast && j >= 0) {
+          const unsigned mp = __ballot_sync(kFull, pass);
+          if (pass) {
+            const int at = ns + __popc(mp & lt);
+            s4[wib][at] = t;
+            sj[wib][at] = (int32_t)j;
+          }
+          ns += __popc(mp);
+          __syncwarp();
+          if (ns >= 32) {
+            if (act) test_stage();
+            __syncwarp();
+            if (lane < ns - 32) {
+              s4[wib][lane] = s4[wib][32 + lane];
+              sj[wib][lane] = sj[wib][32 + lane];
+            }
+            ns -= 32;
+            __syncwarp();
+          }
+        } else {
+          int64_t j = -1;
+          if (kb < take) {
+            const int64_t jj = (int64_t)cand[wib][nc + kb] * kBucket + (lane & 7);
+            if (jj < n && boxid[jj] == b) j = jj;
+          }
+          sj[wib][lane] = (int32_t)j;
+          if (j >= 0) {
             R t[XW];
             load_x(xs, n, j, t);
 #pragma unroll
             for (int a = 0; a < XW; ++a) sx[wib][a][lane] = t[a];
             sh[wib][lane] = hs[j];
           }
-        }
-        __syncwarp();
-        if (act) {
-          if (fast) {
-            // float predicate on the nearest images: no per-pair wrap.  All
-            // 32 staged candidates are tested branch-free into one bit mask
-            // of the union predicate r^2 < max(h_i^2, h_j^2); only the hits
-            // (a few per stage) are then emitted, in candidate order, with
-            // the same r^2 recomputed to tell gather from scatter-only.
-            const float hi2f = (float)hi * (float)hi;
-            uint32_t hit = 0u;
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-              const float4 t = s4[wib][k];
-              const float dx = p[0] - t.x, dy = p[1] - t.y, dz = p[2] - t.z;
-              const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-              hit |= (r2 < fmaxf(hi2f, t.w) ? 1u : 0u) << k;
-            }
-            while (hit) {
-              const int k = __ffs(hit) - 1;
-              hit &= hit - 1u;
-              const int32_t j = sj[wib][k];
-              if (j == s) continue;
-              const float4 t = s4[wib][k];
-              const float dx = p[0] - t.x, dy = p[1] - t.y, dz = p[2] - t.z;
-              const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-              const bool g = r2 < hi2f;
-              const bool sc = r2 < t.w;
-              const uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
-              if (kg + ks < cap_pp) {
-                const int64_t kk = g ? kg : cap_pp - 1 - ks;
-                ell[wbase + kk * 32] = e;
-              }
-              if (g) ++kg; else ++ks;
-            }
-          } else {
+          __syncwarp();
+          if (act) {
             // exact predicate (the oracle's, for the FP64 form)
 #pragma unroll 4
             for (int k = 0; k < 32; ++k) {
@@ -743,9 +768,20 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
               if (g) ++kg; else ++ks;
             }
           }
+          __syncwarp();
         }
-        __syncwarp();
       }
+    }
+    if (fast && ns > 0) {
+      // the last partial stage, padded with slots that never match
+      if (lane >= ns) {
+        s4[wib][lane] = make_float4(__int_as_float(0x7fffffff), 0.f, 0.f, __int_as_float(0x7fffffff));
+        sj[wib][lane] = -1;
+      }
+      __syncwarp();
+      if (act) test_stage();
+      __syncwarp();
+      ns = 0;
     }
     if (overflow) break;
   }
