@@ -95,6 +95,7 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.act_pos = take(2 * 4 * N);
   L.items_r = take(4 * N);
   L.items_a = take(4 * N);
+  L.items_bu = take(4 * N);
   L.total = o;
   return L;
 }

@@ -849,6 +849,34 @@ __global__ void k_csr_fill(const int32_t* __restrict__ perm, const int32_t* __re
   }
 }
 
+// Work list for the union sweeps: within each run of kBalance consecutive
+// sorted particles, the particles ordered by union-list length (longest
+// first, ties by index).  A warp then takes 32 particles of similar length, so
+// fewer of its lanes idle at the end of the walk; every particle still sums
+// its own list in list order, so results are the same bit for bit.
+constexpr int kBalance = 128;
+__global__ void __launch_bounds__(kBalance)
+    k_balance(const int32_t* __restrict__ cnt_g, const int32_t* __restrict__ cnt_s, int64_t n,
+              int32_t* __restrict__ items_u, DevHeader* hdr) {
+  __shared__ int32_t lu[kBalance];
+  const int64_t base = (int64_t)blockIdx.x * kBalance;
+  const int t = threadIdx.x;
+  const int64_t s = base + t;
+  const int m = (int)(n - base < kBalance ? n - base : kBalance);
+  const bool live = t < m;
+  const int u = live ? cnt_g[s] + cnt_s[s] : -1;
+  lu[t] = u;
+  __syncthreads();
+  if (blockIdx.x == 0 && t == 0) hdr->n_all = (int32_t)n;
+  if (!live) return;
+  int ru = 0;
+  for (int k = 0; k < m; ++k) {
+    const int uk = lu[k];
+    ru += (uk > u || (uk == u && k < t)) ? 1 : 0;
+  }
+  items_u[base + ru] = (int32_t)s;
+}
+
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
@@ -925,7 +953,7 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   k_pack_nodes<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, ni, aabb, hmaxn, brange, child,
                                                             nrec);
   ph_tree.end();
-  Phase ph_lists(plan, st, "build.lists", 1);
+  Phase ph_lists(plan, st, "build.lists", 2);
   // neighbor lists (one pass; fixed column of cap_pp slots per particle)
   int32_t* cnt_g = reinterpret_cast<int32_t*>(ws + Ly.cnt_g);
   int32_t* cnt_s = reinterpret_cast<int32_t*>(ws + Ly.cnt_s);
@@ -935,6 +963,8 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   const unsigned gw = (unsigned)((Ly.nw + kNbrWarps - 1) / kNbrWarps);
   k_nbr<R><<<gw, kNbrWarps * 32, 0, st>>>(k0, xs, hs, boxid, wbox, n, nbk, ni, nt, nrec, p4,
                                           cnt_g, cnt_s, wlen_g, wlen_s, ell, Ly.cap_pp, hdr);
+  k_balance<<<(unsigned)((n + kBalance - 1) / kBalance), kBalance, 0, st>>>(
+      cnt_g, cnt_s, n, reinterpret_cast<int32_t*>(ws + Ly.items_bu), hdr);
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }
 

@@ -45,7 +45,8 @@ struct DevHeader {
   unsigned long long nbr_buckets;  // candidate buckets staged by the list build
   int32_t queue[Q_N];
   int32_t n_items[2];  // active-set evaluation: recompute-set and active-set sizes
-  int32_t pad1[14];
+  int32_t n_all;       // length of the length-balanced work lists (= n after a build)
+  int32_t pad1[13];
 };
 
 __device__ __forceinline__ void set_status(DevHeader* h, int code) {
@@ -280,6 +281,8 @@ struct Layout {
   size_t gvs = 0, Ds = 0;
   // active-set evaluation: sorted flags, scan scratch, compacted work lists
   size_t flg = 0, act_pred = 0, act_pos = 0, items_r = 0, items_a = 0;
+  // length-balanced work list of the full union sweeps
+  size_t items_bu = 0;
   // species (0 gas, 1 wind) in sorted order, volume over gas and wind
   size_t spec = 0, Vgws = 0;
   // adjoint

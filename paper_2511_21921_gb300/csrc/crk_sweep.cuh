@@ -19,10 +19,15 @@ struct Common {
   const int32_t* __restrict__ perm;
   int64_t cap_pp;  // list slots per particle: gather part from the front, scatter-only from the back
   int pf;          // prefetch distance in list entries (0 = off)
-  // optional compacted work list (sorted indices; its length on the device):
-  // warps then take 32 listed particles per item instead of 32 consecutive ones
+  // optional compacted work list of the active-set sweeps (sorted indices; its
+  // length on the device): warps then take 32 listed particles per item
+  // instead of 32 consecutive ones
   const int32_t* items = nullptr;
   const int32_t* n_items = nullptr;
+  // the build's length-balanced work list, taken by the full sweeps of passes
+  // with BALANCE set
+  const int32_t* bal = nullptr;
+  const int32_t* n_bal = nullptr;
   // species of the sorted particles (nullptr: all gas) and the volume over
   // gas and wind the volume sweep writes
   const uint8_t* spec = nullptr;
@@ -54,6 +59,8 @@ inline Common make_common(const Plan* plan, char* ws) {
   c.cap_pp = Ly.cap_pp;
   c.pf = plan->p.prefetch;
   c.spec = plan->species ? reinterpret_cast<const uint8_t*>(ws + Ly.spec) : nullptr;
+  c.bal = reinterpret_cast<const int32_t*>(ws + Ly.items_bu);
+  c.n_bal = &c.hdr->n_all;
   c.Vgws = ws + Ly.Vgws;
   return c;
 }
@@ -144,8 +151,9 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
   const int lane = threadIdx.x & 31;
   int32_t* q = &a.c.hdr->queue[P::QUEUE];
   extern __shared__ float4 ring[];
-  const int64_t nlist = a.c.items ? (int64_t)*a.c.n_items : 0;
-  const int64_t nwork = a.c.items ? (nlist + 31) / 32 : a.c.nw;
+  const int32_t* its = a.c.items ? a.c.items : (P::BALANCE ? a.c.bal : nullptr);
+  const int64_t nlist = its ? (int64_t)*(a.c.items ? a.c.n_items : a.c.n_bal) : 0;
+  const int64_t nwork = its ? (nlist + 31) / 32 : a.c.nw;
   for (;;) {
     int w = 0;
     if (lane == 0) w = atomicAdd(q, 1);
@@ -153,9 +161,9 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
     if (w >= nwork) break;
     int64_t s = (int64_t)w * 32 + lane;
     bool live = s < a.c.n;
-    if (a.c.items) {
+    if (its) {
       live = s < nlist;
-      s = live ? a.c.items[s] : 0;
+      s = live ? its[s] : 0;
       if (live && !index_ok(a.c.hdr, s, a.c.n)) live = false, s = 0;
     }
     typename P::State st;
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
       // entry k is evaluated, and the list entry one further ahead.  Unrolled
       // by two so that the buffers alternate without register copies.
       const int tot = lg + ls;
-      const int wmax = P::GATHER && !a.c.items ? a.c.wlen_g[w] : __reduce_max_sync(kFull, tot);
+      const int wmax = P::GATHER && !its ? a.c.wlen_g[w] : __reduce_max_sync(kFull, tot);
       auto raw = [&](int k) -> uint32_t {
         if (k >= tot) return 0u;
         const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
       }
     } else if (P::GATHER) {
       // gather part only: the same row of every lane is one 128-byte line
-      const int wg = a.c.items ? __reduce_max_sync(kFull, lg) : a.c.wlen_g[w];
+      const int wg = its ? __reduce_max_sync(kFull, lg) : a.c.wlen_g[w];
       const int pf = a.c.pf;
       for (int k = 0; k < wg; ++k) {
         if (pf && k + pf < lg)
