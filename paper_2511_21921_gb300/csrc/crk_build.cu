@@ -854,7 +854,7 @@ __global__ void k_csr_fill(const int32_t* __restrict__ perm, const int32_t* __re
 // first, ties by index).  A warp then takes 32 particles of similar length, so
 // fewer of its lanes idle at the end of the walk; every particle still sums
 // its own list in list order, so results are the same bit for bit.
-constexpr int kBalance = 128;
+constexpr int kBalance = 256;
 __global__ void __launch_bounds__(kBalance)
     k_balance(const int32_t* __restrict__ cnt_g, const int32_t* __restrict__ cnt_s, int64_t n,
               int32_t* __restrict__ items_u, DevHeader* hdr) {
