@@ -370,6 +370,15 @@ class Solver:
         return L.crk_autotune(self.plan, _stream(), self._wsp, m.data_ptr(), v.data_ptr(),
                               u.data_ptr(), _ptr(g_dvdt), _ptr(g_dudt), repeats)
 
+    def tune_set(self, choice) -> None:
+        """Set the launch variant of every sweep without timing: ``choice`` is the
+        dict ``autotune`` returned (replaying a stored choice) or eight ints in
+        the order of ``_lib.SWEEPS``."""
+        if isinstance(choice, dict):
+            choice = [choice[k]["variant"] if isinstance(choice[k], dict) else choice[k]
+                      for k in L.SWEEPS]
+        L.crk_tune_set(self.plan, choice)
+
     # -- CUDA graph of a whole step ---------------------------------------------
     def capture(self, fn):
         """Capture ``fn`` (a sequence of this solver's calls with ``check=False``

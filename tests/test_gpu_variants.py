@@ -93,3 +93,23 @@ def test_tune_set_rejects_out_of_range():
     for bad in ([L.CRK_TUNE_VARIANTS] + [0] * 7, [0] * 7 + [-1]):
         with pytest.raises(L.CRKError):
             L.crk_tune_set(s.plan, bad)
+
+
+def test_tune_set_replays_an_autotuner_choice():
+    """A stored autotuner choice, set on a fresh plan, gives the tuned plan's
+    results bit for bit (same kernels, same inputs)."""
+    d = synth.lognormal(12, 1.5, seed=35)
+    n = d["h"].shape[0]
+    t = to_dev(d, "mixed")
+    s1 = Solver(n, 1, "mixed")
+    s1.cell_build(t["x"], t["h"])
+    tuned = s1.autotune(t["m"], t["v"], t["u"], repeats=1)
+    s1.moments(t["m"])
+    r1 = s1.rates(t["v"], t["u"])
+    s2 = Solver(n, 1, "mixed")
+    s2.tune_set(tuned)
+    s2.cell_build(t["x"], t["h"])
+    s2.moments(t["m"])
+    r2 = s2.rates(t["v"], t["u"])
+    torch.cuda.synchronize()
+    assert torch.equal(r1[0], r2[0]) and torch.equal(r1[1], r2[1])
