@@ -130,13 +130,6 @@ __device__ __forceinline__ void prefetch_sources(const typename P::Args& a, uint
     prefetch_record(P::src1(a), j, P::SW1 * (int)sizeof(typename P::Real));
 }
 
-// Persistent sweep: warps pull 32-particle work items from an atomic queue.
-// MINB (minimum resident blocks per SM) sets the register cap and MODE how the
-// neighbor records reach the pair arithmetic: 0 loaded from global memory
-// when the pair is evaluated, 1 copied ahead through the shared-memory ring,
-// 2 loaded one entry ahead into a register double buffer.  Each pass is
-// compiled for three MINB values in each mode and the autotuner picks one of
-// the nine per plan.
 // Register cap that lets MINB blocks of `block` threads share an SM's 64 K
 // registers (a multiple of 8, at most 255).
 constexpr int sweep_regs(int block, int minb) {
@@ -144,6 +137,15 @@ constexpr int sweep_regs(int block, int minb) {
   return r > 255 ? 255 : r;
 }
 
+// Persistent sweep: warps pull 32-particle work items from an atomic queue --
+// 32 consecutive sorted particles, or 32 entries of a work list (the active
+// set's compacted list, or for passes with BALANCE the build's list ordered by
+// union-list length).  MINB (minimum resident blocks per SM) sets the register
+// cap and MODE how the neighbor records reach the pair arithmetic: 0 loaded
+// from global memory when the pair is evaluated, 1 copied ahead through the
+// shared-memory ring, 2 loaded one entry ahead into a register double buffer.
+// Each pass is compiled for three MINB values in each mode and the autotuner
+// picks one of the nine per plan.
 template <class P, int MINB, int MODE>
 __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MINB))
     k_sweep(const typename P::Args a) {
