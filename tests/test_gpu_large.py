@@ -3,9 +3,10 @@ the oracle computes one by one (its lazy target mode):
 
 * clumpy128: 2,097,152 particles, 200 Plummer clumps on a variance-3 lognormal
   background, smoothing lengths spanning about two decades;
-* multibox64: 64 independent boxes of 8^3 .. 96^3 particles in one call.
+* multibox64: 64 independent boxes of 8^3 .. 96^3 particles in one call;
+* lognormal256: the largest configuration, 16.8 M particles in one box.
 
-Both in the mixed form the benchmark runs (float pairs, double-float
+All in the mixed form the benchmark runs (float pairs, double-float
 separations).  These generate a few million particles and take minutes.
 """
 import numpy as np
@@ -88,3 +89,19 @@ def test_multibox64_sampled_parity_mixed():
         err = compare(gb, ora, idx=tg)
         for k in ("dvdt", "dudt"):
             assert err[k] < TOL["mixed"], (b, sizes[b], k, err)
+
+
+def test_lognormal256_sampled_parity_mixed():
+    """The largest configuration: 256^3 = 16,777,216 particles in one box."""
+    d = synth.load("lognormal256")
+    n = d["h"].shape[0]
+    assert n == 256 ** 3
+    gpu, s = run_forward(d, "mixed")
+    assert gpu["status"] == 0
+    tg = _stratified(d["h"], 48, np.random.default_rng(9))
+    ora = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], 1.0, targets=tg)
+    err = compare(gpu, ora, idx=tg)
+    for k in ("dvdt", "dudt"):
+        assert err[k] < TOL["mixed"], (k, err)
+    for k, e in err.items():
+        assert e < 5e-5, (k, err)
