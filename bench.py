@@ -55,9 +55,9 @@ PROFILE_KERNEL = {"b1_volume": "PassB1<float>", "b2_moments": "PassB2<float>",
                   "adj_b1": "PassAB1<float>"}
 
 
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch of ``kernel`` from a committed ncu summary, only if
-    that summary was taken on the current sources (same build digest)."""
+def _profile_of(kernel: str):
+    """(path, metadata, table rows) of the committed ncu summary of ``kernel``,
+    only if it was taken on the current sources (same build digest)."""
     import glob
     from paper_2511_21921_gb300 import build as B
     want = PROFILE_KERNEL.get(kernel)
@@ -65,16 +65,45 @@ def profiled_traffic(kernel: str):
         return None
     digest = B._digest()
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
-        meta = {}
+        meta, rows = {}, {}
         with open(path) as fh:
             for line in fh:
                 if ":" in line and line.split(":", 1)[0] in ("kernel", "build_digest",
                                                             "dram_bytes_per_launch"):
                     k, v = line.split(":", 1)
                     meta[k] = v.strip()
+                elif line.startswith("| ") and line.count("|") == 3:
+                    k, v = [c.strip() for c in line.strip().strip("|").split("|")]
+                    rows[k] = v
         if want in meta.get("kernel", "") and meta.get("build_digest") == digest:
-            return int(meta["dram_bytes_per_launch"])
+            return path, meta, rows
     return None
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of ``kernel`` from a committed ncu summary, only if
+    that summary was taken on the current sources (same build digest)."""
+    p = _profile_of(kernel)
+    return int(p[1]["dram_bytes_per_launch"]) if p else None
+
+
+def profiled_limiter(kernel: str):
+    """The busiest on-chip unit of ``kernel`` in its committed ncu summary (same
+    build digest): L1 throughput, issue activity and FMA-pipe activity, in %."""
+    p = _profile_of(kernel)
+    if not p:
+        return None
+    path, _, rows = p
+
+    def pct(label):
+        v = rows.get(label, "").split()
+        try:
+            return round(float(v[0]), 1)
+        except (IndexError, ValueError):
+            return None
+    return {"l1_throughput_pct": pct("L1 throughput, %"), "issue_active_pct": pct("issue active, %"),
+            "fma_pipe_pct": pct("FMA pipe active, %"),
+            "source": os.path.relpath(path, ROOT)}
 
 
 def _env_int(k, d):
@@ -410,7 +439,8 @@ def run_ours(args, rank, world):
                 "flops_per_pair": FLOPS_PER_PAIR[dom], "pairs": units[UNIT_OF[dom]],
                 "kernel_ms": round(kmean[dom], 4),
                 "frac_of_measured_fp32": round(achieved / alu_peak["fp32_tflops"], 4)
-                if alu_peak["fp32_tflops"] > 0 else None}
+                if alu_peak["fp32_tflops"] > 0 else None,
+                "on_chip": profiled_limiter(dom)}
     res = {
         "metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
