@@ -444,6 +444,7 @@ def run_ours(args, rank, world):
     res = {
         "metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
+        "ms_per_step_median": round(float(np.median(ms)), 4),
         "value": job_pairs / (step_ms * 1e-3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
         "data": "synthetic",
