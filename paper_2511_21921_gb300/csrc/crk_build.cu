@@ -857,7 +857,7 @@ __global__ void k_csr_fill(const int32_t* __restrict__ perm, const int32_t* __re
 constexpr int kBalance = 256;
 __global__ void __launch_bounds__(kBalance)
     k_balance(const int32_t* __restrict__ cnt_g, const int32_t* __restrict__ cnt_s, int64_t n,
-              int32_t* __restrict__ items_u, DevHeader* hdr) {
+              int32_t* __restrict__ items_u, int32_t* __restrict__ cost, DevHeader* hdr) {
   __shared__ int32_t lu[kBalance];
   const int64_t base = (int64_t)blockIdx.x * kBalance;
   const int t = threadIdx.x;
@@ -875,6 +875,45 @@ __global__ void __launch_bounds__(kBalance)
     ru += (uk > u || (uk == u && k < t)) ? 1 : 0;
   }
   items_u[base + ru] = (int32_t)s;
+  // the first (longest) particle of each 32-particle item gives the item's
+  // cost; a partial item (the last one) gets -1
+  if ((ru & 31) == 0) {
+    const int64_t q = (base + ru) >> 5;
+    cost[q] = (base + ru + 32 <= n) ? u : -1;
+  }
+}
+
+// Longest items first.  A persistent sweep ends when its slowest warp finishes
+// its last item, so passes with LPT take the balanced list's items (32
+// particles each) in decreasing order of their longest union list: the last
+// items are the shortest and the warps finish close together.  The order
+// within equal costs does not matter (each particle still sums its own list),
+// and a partial last item stays last.
+constexpr int kLptBins = 1024;
+constexpr int kLptThreads = 1024;
+__global__ void __launch_bounds__(kLptThreads)
+    k_item_sort(const int32_t* __restrict__ cost, int64_t nitems, int32_t* __restrict__ order) {
+  __shared__ int32_t cnt[kLptBins];
+  for (int b = threadIdx.x; b < kLptBins; b += kLptThreads) cnt[b] = 0;
+  __syncthreads();
+  // bin 0 holds the most expensive items, bin kLptBins-1 the partial one
+  auto bin = [](int32_t c) {
+    const int32_t k = c < 0 ? kLptBins - 1 : (kLptBins - 2) - (c < kLptBins - 2 ? c : kLptBins - 2);
+    return k;
+  };
+  for (int64_t q = threadIdx.x; q < nitems; q += kLptThreads) atomicAdd(&cnt[bin(cost[q])], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t run = 0;
+    for (int b = 0; b < kLptBins; ++b) {
+      const int32_t c = cnt[b];
+      cnt[b] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int64_t q = threadIdx.x; q < nitems; q += kLptThreads)
+    order[atomicAdd(&cnt[bin(cost[q])], 1)] = (int32_t)q;
 }
 
 // ---------------------------------------------------------------------------
@@ -953,7 +992,7 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   k_pack_nodes<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, ni, aabb, hmaxn, brange, child,
                                                             nrec);
   ph_tree.end();
-  Phase ph_lists(plan, st, "build.lists", 2);
+  Phase ph_lists(plan, st, "build.lists", 3);
   // neighbor lists (one pass; fixed column of cap_pp slots per particle)
   int32_t* cnt_g = reinterpret_cast<int32_t*>(ws + Ly.cnt_g);
   int32_t* cnt_s = reinterpret_cast<int32_t*>(ws + Ly.cnt_s);
@@ -963,8 +1002,11 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   const unsigned gw = (unsigned)((Ly.nw + kNbrWarps - 1) / kNbrWarps);
   k_nbr<R><<<gw, kNbrWarps * 32, 0, st>>>(k0, xs, hs, boxid, wbox, n, nbk, ni, nt, nrec, p4,
                                           cnt_g, cnt_s, wlen_g, wlen_s, ell, Ly.cap_pp, hdr);
+  int32_t* cost = reinterpret_cast<int32_t*>(ws + Ly.item_cost);
   k_balance<<<(unsigned)((n + kBalance - 1) / kBalance), kBalance, 0, st>>>(
-      cnt_g, cnt_s, n, reinterpret_cast<int32_t*>(ws + Ly.items_bu), hdr);
+      cnt_g, cnt_s, n, reinterpret_cast<int32_t*>(ws + Ly.items_bu), cost, hdr);
+  k_item_sort<<<1, kLptThreads, 0, st>>>(cost, Ly.nw,
+                                         reinterpret_cast<int32_t*>(ws + Ly.item_order));
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }
 

@@ -281,8 +281,9 @@ struct Layout {
   size_t gvs = 0, Ds = 0;
   // active-set evaluation: sorted flags, scan scratch, compacted work lists
   size_t flg = 0, act_pred = 0, act_pos = 0, items_r = 0, items_a = 0;
-  // length-balanced work list of the full union sweeps
-  size_t items_bu = 0;
+  // length-balanced work list of the full union sweeps, the cost of each of
+  // its 32-particle items and the items' longest-first order
+  size_t items_bu = 0, item_cost = 0, item_order = 0;
   // species (0 gas, 1 wind) in sorted order, volume over gas and wind
   size_t spec = 0, Vgws = 0;
   // adjoint

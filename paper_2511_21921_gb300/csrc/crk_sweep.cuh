@@ -25,9 +25,10 @@ struct Common {
   const int32_t* items = nullptr;
   const int32_t* n_items = nullptr;
   // the build's length-balanced work list, taken by the full sweeps of passes
-  // with BALANCE set
+  // with BALANCE set; passes with LPT also take its items longest first
   const int32_t* bal = nullptr;
   const int32_t* n_bal = nullptr;
+  const int32_t* bal_order = nullptr;
   // species of the sorted particles (nullptr: all gas) and the volume over
   // gas and wind the volume sweep writes
   const uint8_t* spec = nullptr;
@@ -60,6 +61,7 @@ inline Common make_common(const Plan* plan, char* ws) {
   c.pf = plan->p.prefetch;
   c.spec = plan->species ? reinterpret_cast<const uint8_t*>(ws + Ly.spec) : nullptr;
   c.bal = reinterpret_cast<const int32_t*>(ws + Ly.items_bu);
+  c.bal_order = reinterpret_cast<const int32_t*>(ws + Ly.item_order);
   c.n_bal = &c.hdr->n_all;
   c.Vgws = ws + Ly.Vgws;
   return c;
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
     int64_t s = (int64_t)w * 32 + lane;
     bool live = s < a.c.n;
     if (its) {
+      if (P::LPT && !a.c.items) s = (int64_t)a.c.bal_order[w] * 32 + lane;
       live = s < nlist;
       s = live ? its[s] : 0;
       if (live && !index_ok(a.c.hdr, s, a.c.n)) live = false, s = 0;
