@@ -903,14 +903,31 @@ __global__ void __launch_bounds__(kLptThreads)
   };
   for (int64_t q = threadIdx.x; q < nitems; q += kLptThreads) atomicAdd(&cnt[bin(cost[q])], 1);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int32_t run = 0;
-    for (int b = 0; b < kLptBins; ++b) {
-      const int32_t c = cnt[b];
-      cnt[b] = run;
-      run += c;
-    }
+  // exclusive scan of the bin counts (one bin per thread)
+  static_assert(kLptBins == kLptThreads, "one bin per thread");
+  __shared__ int32_t wsum[kLptThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int32_t v = cnt[threadIdx.x];
+  int32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t t = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += t;
   }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const int32_t w0 = wsum[lane];
+    int32_t winc = w0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t t = __shfl_up_sync(kFull, winc, o);
+      if (lane >= o) winc += t;
+    }
+    wsum[lane] = winc - w0;
+  }
+  __syncthreads();
+  cnt[threadIdx.x] = wsum[wid] + inc - v;
   __syncthreads();
   for (int64_t q = threadIdx.x; q < nitems; q += kLptThreads)
     order[atomicAdd(&cnt[bin(cost[q])], 1)] = (int32_t)q;
