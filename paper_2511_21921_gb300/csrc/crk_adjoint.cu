@@ -226,7 +226,7 @@ template <class R> struct PassA2 {
   static constexpr int QUEUE = Q_A_C2;
   using Real = R;
   static constexpr int SW0 = Rec<R>::C2, SW1 = 4;  // words staged per neighbor
-  static constexpr bool LPT = true;  // balanced items longest first
+  static constexpr bool LPT = true;   // items longest first
   static constexpr bool BALANCE = true;   // full sweep takes the length-balanced work list
   using RC = Rec<R>;
   using AR = ARec<R>;
@@ -506,7 +506,7 @@ template <class R> struct PassA1 {
   static constexpr int QUEUE = Q_A_C1;
   using Real = R;
   static constexpr int SW0 = ARec<R>::A1, SW1 = 0;  // words staged per neighbor
-  static constexpr bool LPT = false;  // balanced items longest first
+  static constexpr bool LPT = false;  // queue order (longest first measured slower here)
   static constexpr bool BALANCE = true;   // full sweep takes the length-balanced work list
   using AR = ARec<R>;
   struct Args {
@@ -669,7 +669,7 @@ template <class R> struct PassAB2 {
   static constexpr int QUEUE = Q_A_B2;
   using Real = R;
   static constexpr int SW0 = ARec<R>::A2, SW1 = 0;  // words staged per neighbor
-  static constexpr bool LPT = false;  // balanced items longest first
+  static constexpr bool LPT = false;  // queue order (longest first measured slower here)
   static constexpr bool BALANCE = true;   // full sweep takes the length-balanced work list
   using AR = ARec<R>;
   struct Args {
@@ -816,7 +816,7 @@ template <class R> struct PassAB1 {
   static constexpr int QUEUE = Q_A_B1;
   using Real = R;
   static constexpr int SW0 = ARec<R>::A3, SW1 = 0;  // words staged per neighbor
-  static constexpr bool LPT = false;  // balanced items longest first
+  static constexpr bool LPT = true;   // items longest first
   static constexpr bool BALANCE = false;  // full sweep takes 32 consecutive particles per warp
   using AR = ARec<R>;
   struct Args {

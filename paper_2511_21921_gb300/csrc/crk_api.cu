@@ -98,6 +98,8 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.items_bu = take(4 * N);
   L.item_cost = take(4 * NW + 4);
   L.item_order = take(4 * NW + 4);
+  L.seq_cost = take(4 * NW + 4);
+  L.seq_order = take(4 * NW + 4);
   L.total = o;
   return L;
 }

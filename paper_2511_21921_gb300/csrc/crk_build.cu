@@ -857,7 +857,8 @@ __global__ void k_csr_fill(const int32_t* __restrict__ perm, const int32_t* __re
 constexpr int kBalance = 256;
 __global__ void __launch_bounds__(kBalance)
     k_balance(const int32_t* __restrict__ cnt_g, const int32_t* __restrict__ cnt_s, int64_t n,
-              int32_t* __restrict__ items_u, int32_t* __restrict__ cost, DevHeader* hdr) {
+              int32_t* __restrict__ items_u, int32_t* __restrict__ cost,
+              int32_t* __restrict__ seq_cost, DevHeader* hdr) {
   __shared__ int32_t lu[kBalance];
   const int64_t base = (int64_t)blockIdx.x * kBalance;
   const int t = threadIdx.x;
@@ -866,6 +867,14 @@ __global__ void __launch_bounds__(kBalance)
   const bool live = t < m;
   const int u = live ? cnt_g[s] + cnt_s[s] : -1;
   lu[t] = u;
+  // cost of the item of 32 consecutive particles this warp covers (-1 when partial)
+  {
+    int um = u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) um = max(um, __shfl_xor_sync(kFull, um, o));
+    const int64_t q = s >> 5;
+    if ((t & 31) == 0 && q * 32 < n) seq_cost[q] = (q * 32 + 32 <= n) ? um : -1;
+  }
   __syncthreads();
   if (blockIdx.x == 0 && t == 0) hdr->n_all = (int32_t)n;
   if (!live) return;
@@ -1009,7 +1018,7 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   k_pack_nodes<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, ni, aabb, hmaxn, brange, child,
                                                             nrec);
   ph_tree.end();
-  Phase ph_lists(plan, st, "build.lists", 3);
+  Phase ph_lists(plan, st, "build.lists", 4);
   // neighbor lists (one pass; fixed column of cap_pp slots per particle)
   int32_t* cnt_g = reinterpret_cast<int32_t*>(ws + Ly.cnt_g);
   int32_t* cnt_s = reinterpret_cast<int32_t*>(ws + Ly.cnt_s);
@@ -1020,10 +1029,13 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   k_nbr<R><<<gw, kNbrWarps * 32, 0, st>>>(k0, xs, hs, boxid, wbox, n, nbk, ni, nt, nrec, p4,
                                           cnt_g, cnt_s, wlen_g, wlen_s, ell, Ly.cap_pp, hdr);
   int32_t* cost = reinterpret_cast<int32_t*>(ws + Ly.item_cost);
+  int32_t* seq_cost = reinterpret_cast<int32_t*>(ws + Ly.seq_cost);
   k_balance<<<(unsigned)((n + kBalance - 1) / kBalance), kBalance, 0, st>>>(
-      cnt_g, cnt_s, n, reinterpret_cast<int32_t*>(ws + Ly.items_bu), cost, hdr);
+      cnt_g, cnt_s, n, reinterpret_cast<int32_t*>(ws + Ly.items_bu), cost, seq_cost, hdr);
   k_item_sort<<<1, kLptThreads, 0, st>>>(cost, Ly.nw,
                                          reinterpret_cast<int32_t*>(ws + Ly.item_order));
+  k_item_sort<<<1, kLptThreads, 0, st>>>(seq_cost, Ly.nw,
+                                         reinterpret_cast<int32_t*>(ws + Ly.seq_order));
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }
 

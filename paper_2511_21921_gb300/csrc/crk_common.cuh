@@ -284,6 +284,8 @@ struct Layout {
   // length-balanced work list of the full union sweeps, the cost of each of
   // its 32-particle items and the items' longest-first order
   size_t items_bu = 0, item_cost = 0, item_order = 0;
+  // the same for the items of 32 consecutive particles
+  size_t seq_cost = 0, seq_order = 0;
   // species (0 gas, 1 wind) in sorted order, volume over gas and wind
   size_t spec = 0, Vgws = 0;
   // adjoint

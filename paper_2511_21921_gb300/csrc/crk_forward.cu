@@ -40,7 +40,7 @@ template <class R> struct PassB1 {
   static constexpr int QUEUE = Q_B1;
   using Real = R;
   static constexpr int SW0 = Rec<R>::B1, SW1 = 0;  // words staged per neighbor
-  static constexpr bool LPT = false;  // balanced items longest first
+  static constexpr bool LPT = false;  // queue order (longest first gained nothing here)
   static constexpr bool BALANCE = false;  // full sweep takes 32 consecutive particles per warp
   using RC = Rec<R>;
   struct Args {
@@ -115,7 +115,7 @@ template <class R> struct PassB2 {
   static constexpr int QUEUE = Q_B2;
   using Real = R;
   static constexpr int SW0 = Rec<R>::B2, SW1 = 0;  // words staged per neighbor
-  static constexpr bool LPT = false;  // balanced items longest first
+  static constexpr bool LPT = false;  // queue order (longest first gained nothing here)
   static constexpr bool BALANCE = false;  // full sweep takes 32 consecutive particles per warp
   using RC = Rec<R>;
   struct Args {
@@ -238,7 +238,7 @@ template <class R> struct PassC1 {
   static constexpr int QUEUE = Q_C1;
   using Real = R;
   static constexpr int SW0 = Rec<R>::C1, SW1 = 0;  // words staged per neighbor
-  static constexpr bool LPT = false;  // balanced items longest first
+  static constexpr bool LPT = false;  // queue order (longest first gained nothing here)
   static constexpr bool BALANCE = false;  // full sweep takes 32 consecutive particles per warp
   using RC = Rec<R>;
   struct Args {
@@ -363,7 +363,7 @@ template <class R> struct PassC2 {
   static constexpr int QUEUE = Q_C2;
   using Real = R;
   static constexpr int SW0 = Rec<R>::C2, SW1 = 0;  // words staged per neighbor
-  static constexpr bool LPT = true;  // balanced items longest first
+  static constexpr bool LPT = true;   // items longest first
   static constexpr bool BALANCE = true;   // full sweep takes the length-balanced work list
   using RC = Rec<R>;
   struct Args {

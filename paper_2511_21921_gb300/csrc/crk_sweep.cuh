@@ -29,6 +29,9 @@ struct Common {
   const int32_t* bal = nullptr;
   const int32_t* n_bal = nullptr;
   const int32_t* bal_order = nullptr;
+  // longest-first order of the items of 32 consecutive particles (passes with
+  // LPT and without BALANCE)
+  const int32_t* seq_order = nullptr;
   // species of the sorted particles (nullptr: all gas) and the volume over
   // gas and wind the volume sweep writes
   const uint8_t* spec = nullptr;
@@ -62,6 +65,7 @@ inline Common make_common(const Plan* plan, char* ws) {
   c.spec = plan->species ? reinterpret_cast<const uint8_t*>(ws + Ly.spec) : nullptr;
   c.bal = reinterpret_cast<const int32_t*>(ws + Ly.items_bu);
   c.bal_order = reinterpret_cast<const int32_t*>(ws + Ly.item_order);
+  c.seq_order = reinterpret_cast<const int32_t*>(ws + Ly.seq_order);
   c.n_bal = &c.hdr->n_all;
   c.Vgws = ws + Ly.Vgws;
   return c;
@@ -163,7 +167,9 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
     if (lane == 0) w = atomicAdd(q, 1);
     w = __shfl_sync(kFull, w, 0);
     if (w >= nwork) break;
-    int64_t s = (int64_t)w * 32 + lane;
+    // the item this warp takes (items of consecutive particles may be reordered)
+    const int64_t wi = (P::LPT && !P::BALANCE && !a.c.items) ? a.c.seq_order[w] : w;
+    int64_t s = wi * 32 + lane;
     bool live = s < a.c.n;
     if (its) {
       if (P::LPT && !a.c.items) s = (int64_t)a.c.bal_order[w] * 32 + lane;
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
       // entry k is evaluated, and the list entry one further ahead.  Unrolled
       // by two so that the buffers alternate without register copies.
       const int tot = lg + ls;
-      const int wmax = P::GATHER && !its ? a.c.wlen_g[w] : __reduce_max_sync(kFull, tot);
+      const int wmax = P::GATHER && !its ? a.c.wlen_g[wi] : __reduce_max_sync(kFull, tot);
       auto raw = [&](int k) -> uint32_t {
         if (k >= tot) return 0u;
         const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
@@ -242,7 +248,7 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
       }
     } else if (P::GATHER) {
       // gather part only: the same row of every lane is one 128-byte line
-      const int wg = its ? __reduce_max_sync(kFull, lg) : a.c.wlen_g[w];
+      const int wg = its ? __reduce_max_sync(kFull, lg) : a.c.wlen_g[wi];
       const int pf = a.c.pf;
       for (int k = 0; k < wg; ++k) {
         if (pf && k + pf < lg)
