@@ -812,7 +812,7 @@ template <class R> struct PassAB2 {
 template <class R> struct PassAB1 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
-  static constexpr int MB0 = 1, MB1 = 1, MB2 = 1;  // resident-block variants
+  static constexpr int MB0 = 1, MB1 = 14, MB2 = 16;  // resident-block variants
   static constexpr int QUEUE = Q_A_B1;
   using Real = R;
   static constexpr int SW0 = ARec<R>::A3, SW1 = 0;  // words staged per neighbor

@@ -1018,7 +1018,8 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   k_pack_nodes<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, ni, aabb, hmaxn, brange, child,
                                                             nrec);
   ph_tree.end();
-  Phase ph_lists(plan, st, "build.lists", 4);
+  Phase ph_lists(plan, st, "build.lists",
+                 lpt_worthwhile(Ly.nw, (int64_t)plan->num_sms * 64) ? 4 : 2);
   // neighbor lists (one pass; fixed column of cap_pp slots per particle)
   int32_t* cnt_g = reinterpret_cast<int32_t*>(ws + Ly.cnt_g);
   int32_t* cnt_s = reinterpret_cast<int32_t*>(ws + Ly.cnt_s);
@@ -1032,10 +1033,12 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   int32_t* seq_cost = reinterpret_cast<int32_t*>(ws + Ly.seq_cost);
   k_balance<<<(unsigned)((n + kBalance - 1) / kBalance), kBalance, 0, st>>>(
       cnt_g, cnt_s, n, reinterpret_cast<int32_t*>(ws + Ly.items_bu), cost, seq_cost, hdr);
-  k_item_sort<<<1, kLptThreads, 0, st>>>(cost, Ly.nw,
-                                         reinterpret_cast<int32_t*>(ws + Ly.item_order));
-  k_item_sort<<<1, kLptThreads, 0, st>>>(seq_cost, Ly.nw,
-                                         reinterpret_cast<int32_t*>(ws + Ly.seq_order));
+  if (lpt_worthwhile(Ly.nw, (int64_t)plan->num_sms * 64)) {
+    k_item_sort<<<1, kLptThreads, 0, st>>>(cost, Ly.nw,
+                                           reinterpret_cast<int32_t*>(ws + Ly.item_order));
+    k_item_sort<<<1, kLptThreads, 0, st>>>(seq_cost, Ly.nw,
+                                           reinterpret_cast<int32_t*>(ws + Ly.seq_order));
+  }
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }
 

@@ -61,6 +61,15 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb);
 template <class T>
 void exclusive_scan(const T* in, T* out, int64_t n, void* tmp, T* total_out, cudaStream_t st);
 int scan_launches(int64_t n);  // kernels exclusive_scan launches for n elements
+// Longest-first item orders pay off only while a warp takes few items (the
+// tail is a large share of the sweep); with many items per warp the queue
+// order's locality wins.  A sweep uses them when it has at most this many
+// 32-particle items per resident warp, and the build sorts them only when
+// some sweep can.
+constexpr int kLptItemsPerWarp = 8;
+inline bool lpt_worthwhile(int64_t items, int64_t warps) {
+  return items <= (int64_t)kLptItemsPerWarp * warps;
+}
 
 template <class R>
 crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int32_t nb,

@@ -32,6 +32,7 @@ struct Common {
   // longest-first order of the items of 32 consecutive particles (passes with
   // LPT and without BALANCE)
   const int32_t* seq_order = nullptr;
+  bool lpt = false;  // set per launch: this sweep takes items longest first
   // species of the sorted particles (nullptr: all gas) and the volume over
   // gas and wind the volume sweep writes
   const uint8_t* spec = nullptr;
@@ -168,11 +169,11 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
     w = __shfl_sync(kFull, w, 0);
     if (w >= nwork) break;
     // the item this warp takes (items of consecutive particles may be reordered)
-    const int64_t wi = (P::LPT && !P::BALANCE && !a.c.items) ? a.c.seq_order[w] : w;
+    const int64_t wi = (P::LPT && !P::BALANCE && a.c.lpt && !a.c.items) ? a.c.seq_order[w] : w;
     int64_t s = wi * 32 + lane;
     bool live = s < a.c.n;
     if (its) {
-      if (P::LPT && !a.c.items) s = (int64_t)a.c.bal_order[w] * 32 + lane;
+      if (P::LPT && a.c.lpt && !a.c.items) s = (int64_t)a.c.bal_order[w] * 32 + lane;
       live = s < nlist;
       s = live ? its[s] : 0;
       if (live && !index_ok(a.c.hdr, s, a.c.n)) live = false, s = 0;
@@ -514,7 +515,9 @@ void launch_variant(Plan* plan, cudaStream_t st, const typename P::Args& a) {
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int grid = sweep_grid(plan, fn, P::BLOCK, (int)smem);
-  k_sweep<P, MB, MODE><<<grid, P::BLOCK, smem, st>>>(a);
+  typename P::Args b = a;
+  b.c.lpt = P::LPT && lpt_worthwhile(plan->ly.nw, (int64_t)grid * P::BLOCK / 32);
+  k_sweep<P, MB, MODE><<<grid, P::BLOCK, smem, st>>>(b);
 }
 
 // Variant v of a sweep: v % 3 picks the resident-block count (MB0..MB2),
