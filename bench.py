@@ -254,8 +254,8 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     ms_eager = timed(lambda: step(dv), max(3, args.steps // 4))
 
-    sampler = ClockSampler(dev.index, out_dir=os.path.join(ROOT, "gpurun_out") if
-                           os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    # CRK_CLOCKS_DIR (optional): a folder that receives the raw clock samples
+    sampler = ClockSampler(dev.index, out_dir=os.environ.get("CRK_CLOCKS_DIR") or None)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
