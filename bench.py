@@ -160,12 +160,14 @@ class ClockSampler:
                 except ValueError:
                     continue
                 rows.append((sm, smax, parts[5], parts[6], parts[7], parts[8]))
-        if self.out_dir:
-            try:
+        try:
+            if self.out_dir:
                 os.makedirs(self.out_dir, exist_ok=True)
                 os.replace(self.path, os.path.join(self.out_dir, "clocks.csv"))
-            except OSError:
-                pass
+            else:
+                os.remove(self.path)
+        except OSError:
+            pass
         if not rows:
             return None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
