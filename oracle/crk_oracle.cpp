@@ -28,6 +28,16 @@
 // template parameter; instantiating it with a forward-mode dual number gives a
 // Jacobian-vector product of the whole chain with no separate derivative code.
 //
+// Pins (tests/): kernel quadrature and derivative, brute-force neighbor sets,
+// reproduction identities, lattice symmetries, exact gradients of linear
+// fields, conservation with equal and unequal masses, the mass linearity of
+// the volume and the closed-form density on a two-species lattice, the
+// standard-SPH reduction, and the linear-field limiter tests (phi(1) = 1, the
+// limited relative velocity vanishes, damping only below eta_crit).
+// Parity unpinned: the shape of the limiter phi(r) away from r = 1 and the
+// viscosity constants are readings of the cited formulation, fixed by no
+// printed value; the GPU path must match this file there.
+//
 // Plainness: every stage is the definition written out as a loop over the
 // neighbor set of one particle.  Neighbor sets come from brute force (O(N^2))
 // or from a simple k-d tree whose leaves apply the same exact predicate; the

@@ -23,11 +23,15 @@ _lock = threading.Lock()
 _lib = None
 
 # Every oracle function has a pin in tests/ (invariants, special cases, brute
-# force, quadrature or finite differences).  The absolute values of the rates
-# beyond those invariants rest on the reading of the formulation the paper
-# defers (limiter constants, where Q enters); that part is "parity unpinned".
-PARITY_UNPINNED = ("absolute rate values beyond conservation, lattice, "
-                   "inviscid-limit and standard-SPH reductions")
+# force, quadrature, finite differences, the linear-field and two-species
+# lattice reductions).  What no pin fixes: the shape of the limiter function
+# phi(r) away from r = 1 (4r/(1+r)^2, a reading of the formulation the paper
+# defers to; phi(1) = 1, the limited relative velocity and the side of the
+# near-field damping threshold are pinned), the viscosity constants, and so
+# the absolute rate values beyond the invariants and reductions.
+PARITY_UNPINNED = ("limiter shape phi(r) for r != 1 and the viscosity constants; absolute "
+                   "rate values beyond conservation (equal and unequal masses), lattice, "
+                   "linear-field, inviscid-limit and standard-SPH reductions")
 
 STATUS = {0: "ok", 1: "invalid argument", 4: "domain (x outside [0,L) or h >= L/2)",
           5: "non-finite input", 6: "singular second moment"}

@@ -9,7 +9,9 @@ and returns a dict with float64 arrays ``x`` (3, n) in ``[0, L)``, ``v`` (3, n),
 ``u`` (n,), ``h`` (n,), ``m`` (n,) and the box side ``L``; multi-box sets also
 carry ``box_off`` (B+1,) and ``box_L`` (B,).
 
-Workload shapes (periodic unit boxes, equal masses m = 1/N):
+Workload shapes (periodic unit boxes, equal masses m = 1/N; the workloads
+named with a trailing ``m`` are the same boxes with lognormal masses, see
+``unequal_masses``):
 
 * ``lattice``  -- 16^3 cubic lattice jittered by U(-0.2, 0.2) spacing, constant
   h for about 64 neighbors, v ~ N(0, 0.1), u ~ lognormal(0, 0.5).
@@ -193,6 +195,18 @@ def cotangents(n, seed=4):
     return rng.standard_normal((3, n)), rng.standard_normal(n)
 
 
+def unequal_masses(d, seed=6, sigma=0.7, cut=2.5):
+    """A copy of workload ``d`` whose masses are lognormal: ln(m N) ~ N(0, sigma)
+    truncated at ``cut`` sigma (a spread of exp(2 cut sigma) = 33x for the
+    defaults), everything else unchanged.  Equal masses hide where m_i and m_j
+    enter the sums; these inputs exercise them."""
+    rng = np.random.default_rng(seed)
+    out = dict(d)
+    n = d["h"].shape[0]
+    out["m"] = np.exp(_truncated_normal(rng, n, sigma, cut)) / n
+    return out
+
+
 # --------------------------------------------------------------------------
 # named workloads with an on-disk cache (generation of the large ones takes
 # tens of seconds because of the nearest-neighbor queries)
@@ -205,6 +219,10 @@ WORKLOADS = {
     "clumpy128": lambda: clumpy(128, seed=2),
     "multibox64": lambda: multibox(64),
     "lognormal256": lambda: lognormal(256, 1.5, seed=5),
+    # the same boxes with lognormal masses (33x spread)
+    "lattice16m": lambda: unequal_masses(lattice(16, seed=0), seed=6),
+    "lognormal32m": lambda: unequal_masses(lognormal(32, 1.5, seed=3), seed=6),
+    "lognormal64m": lambda: unequal_masses(lognormal(64, 1.5, seed=1), seed=7),
 }
 
 
