@@ -115,16 +115,32 @@ def _env_int(k, d):
 
 # ---------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of SM clock and throttle reasons during a region.
+
+    The GPU is addressed by its UUID (``nvidia-smi --id`` uses the physical
+    numbering, which CUDA_VISIBLE_DEVICES does not change), and only samples
+    whose timestamps fall between ``mark_start`` and ``mark_stop`` count."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index=0, out_dir=None):
+    def __init__(self, device=None, out_dir=None):
         self.proc = None
-        self.gpu = gpu_index
+        self.gpu = self.device_id(device)
         self.path = None
         self.out_dir = out_dir
+        self.t0 = self.t1 = None
+
+    @staticmethod
+    def device_id(device):
+        """UUID of a torch device in the form nvidia-smi takes (GPU-...), or
+        the index when the UUID is not available."""
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(device).uuid)
+            return u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            return str(getattr(device, "index", 0) or 0)
 
     def start(self):
         try:
@@ -137,6 +153,22 @@ class ClockSampler:
             time.sleep(0.3)
         except Exception:
             self.proc = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_stop(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _when(ts):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(ts.strip(), fmt).timestamp()
+            except ValueError:
+                pass
+        return None
 
     def stop(self):
         if self.proc is None:
@@ -152,14 +184,14 @@ class ClockSampler:
         with open(self.path) as fh:
             for line in fh.read().splitlines()[1:]:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
+                if len(parts) < 10:
                     continue
                 try:
-                    sm = float(parts[1].split()[0])
-                    smax = float(parts[2].split()[0])
+                    sm = float(parts[2].split()[0])
+                    smax = float(parts[3].split()[0])
                 except ValueError:
                     continue
-                rows.append((sm, smax, parts[5], parts[6], parts[7], parts[8]))
+                rows.append((self._when(parts[0]), sm, smax, parts[6], parts[7], parts[8], parts[9]))
         try:
             if self.out_dir:
                 os.makedirs(self.out_dir, exist_ok=True)
@@ -170,11 +202,17 @@ class ClockSampler:
             pass
         if not rows:
             return None
+        inside = [r for r in rows if r[0] is not None and self.t0 is not None and
+                  self.t1 is not None and self.t0 <= r[0] <= self.t1]
+        use = inside if inside else rows
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k] == "Active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows),
-                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
-                "samples": len(rows)}
+        reasons = sorted({names[k] for r in use for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(r[1] for r in use),
+                "sm_max_mhz": max(r[2] for r in use), "reasons": reasons,
+                "samples": len(rows), "samples_in_timed_region": len(inside),
+                "gpu": self.gpu,
+                "region": "samples inside the timed region" if inside else
+                          "no sample fell inside the timed region: all samples"}
 
 
 # ---------------------------------------------------------------------------- GPU arm
@@ -257,12 +295,14 @@ def run_ours(args, rank, world):
     ms_eager = timed(lambda: step(dv), max(3, args.steps // 4))
 
     # CRK_CLOCKS_DIR (optional): a folder that receives the raw clock samples
-    sampler = ClockSampler(dev.index, out_dir=os.environ.get("CRK_CLOCKS_DIR") or None)
+    sampler = ClockSampler(dev, out_dir=os.environ.get("CRK_CLOCKS_DIR") or None)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    sampler.mark_start()
     ms = timed(run, args.steps)
+    sampler.mark_stop()
     launches = per_step_launches * args.steps
     clocks = sampler.stop()
     torch.cuda.synchronize()

@@ -443,22 +443,27 @@ crk_status crk_alu_peak(crk_stream_t stream, int32_t fp64, int32_t iters, double
  * callers that cannot allocate device memory -- for example a subgrid operator
  * called from inside a simulation framework whose device-memory pool owns all
  * allocations, or a host loop that must not call cudaMalloc/cudaFree because
- * they can synchronise the device.  It gives the same volume as crk_cell_build
- * followed by crk_moments (V_out), for at most CRK_STATIC_MAX_PARTICLES
- * particles, using a fixed scratch area of about 2.6 MB that is compiled into
- * the library and that every GPU loading the library keeps until exit.
+ * they can synchronise the device.  For particles that are all gas (no
+ * species) and all inside [0, L) it gives the volume of crk_cell_build
+ * followed by crk_moments (V_out), to rounding (the summation order differs),
+ * for at most CRK_STATIC_MAX_PARTICLES particles, using a fixed scratch area of
+ * about 2.6 MB that is compiled into the library and that every GPU loading
+ * the library keeps until exit.
  *   precision: CRK_FP64 (h, m, V_out double) or CRK_MIXED32 (float).
  *   n: particles, 0 <= n <= CRK_STATIC_MAX_PARTICLES, else CRK_ENOMEM.
  *   L: box side; x: device double[3][n] in [0, L); h, m, V_out: device real[n].
  *   h_bound: host upper estimate of max h; it only sets the cell size (at most
- *   32 cells per axis), any positive value gives the same result.
- * Particles with x outside [0, L) or h outside (0, L/2) get V = NaN.  The call
- * allocates nothing and is asynchronous on `stream`.  The first call on each
- * device looks up the scratch address (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  All calls share the scratch, which
- * keeps the last call's contents (each call clears what it needs), so calls
- * whose kernels overlap on the GPU -- on different streams or host threads --
- * race and must be serialised by the caller. */
+ *   32 cells per axis), any positive value gives the same result to rounding.
+ * A particle with x outside [0, L) gets V = NaN and enters no other
+ * particle's sum; a particle with h outside (0, L/2) gets V = NaN and still
+ * enters its neighbors' sums.  The call allocates nothing and is asynchronous
+ * on `stream`.  The first call on each device looks up the scratch address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture;
+ * the address is kept for the life of the process, so a cudaDeviceReset of
+ * that device must not come between two calls.  All calls share the scratch,
+ * which keeps the last call's contents (each call clears what it needs), so
+ * calls whose kernels overlap on the GPU -- on different streams or host
+ * threads -- race and must be serialised by the caller. */
 #define CRK_STATIC_MAX_PARTICLES 65536
 crk_status crk_volume_static(crk_stream_t stream, int32_t precision, int64_t n, double L,
                              double h_bound, const double* x, const void* h, const void* m,

@@ -450,6 +450,33 @@ __device__ __forceinline__ float norm2(const float* d) {
 __device__ __forceinline__ double sq(double a) { return __dmul_rn(a, a); }
 __device__ __forceinline__ float sq(float a) { return a * a; }
 
+// Exact pair predicate of the mixed form.  The float candidate test works on
+// positions rounded to float (and, for the nearest-image staging, shifted by a
+// float L), so r^2 carries an error of at most 2^-24 (10 sqrt(3) L r + 6 r^2)
+// against the double r^2 of the caller's positions (each coordinate within
+// 5 * 2^-24 L of its exact image difference, three roundings in the sum of
+// squares, one in h^2).  A decision r^2 < h^2 is therefore certain outside the
+// band |r^2 - h^2| <= tol(h) below (wider by a third in the L term and more in
+// the h^2 term); inside it the pair is decided again in double exactly as the
+// definition states -- minimum image decided and formed in double, r^2 summed
+// without contraction, compared with the squared (float) smoothing lengths --
+// so the mixed lists equal the FP64 lists of the same inputs.
+__device__ __forceinline__ float list_band(float h, float L) {
+  return 5.9604645e-8f * fmaf(16.f * h, h, 24.f * L * h);
+}
+__device__ __forceinline__ double exact_r2(const double* __restrict__ xd, int64_t n, int64_t pi,
+                                           int64_t pj, double L) {
+  const double a[3] = {xd[pi], xd[n + pi], xd[2 * n + pi]};
+  const double b[3] = {xd[pj], xd[n + pj], xd[2 * n + pj]};
+  double d[3];
+  separation(a, b, L, 0.5 * L, d);
+  return norm2(d);
+}
+// 1: certainly inside (r^2 < h^2), 0: certainly outside, -1: within the band
+__device__ __forceinline__ int band_decide(float r2, float h2, float tol) {
+  return r2 < h2 - tol ? 1 : (r2 > h2 + tol ? 0 : -1);
+}
+
 // One warp per 32 consecutive sorted particles walks the tree once for the
 // whole group (separately for each box present in the group): nodes are
 // tested 32 at a time against the group's bounding box grown by
@@ -493,13 +520,18 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
     const int32_t* __restrict__ boxid,
     const double* __restrict__ box_L, int64_t n, int64_t nbk, int64_t ni, int64_t nt,
     const float* __restrict__ nrec, const float4* __restrict__ p4, int32_t* __restrict__ cnt_g, int32_t* __restrict__ cnt_s, int32_t* __restrict__ wlen_g,
-    int32_t* __restrict__ wlen_s, uint32_t* __restrict__ ell, int64_t cap_pp, DevHeader* hdr) {
+    int32_t* __restrict__ wlen_s, uint32_t* __restrict__ ell, int64_t cap_pp, DevHeader* hdr,
+    const double* __restrict__ xd, const int32_t* __restrict__ perm) {
   constexpr int XW = Prec<R>::XW;
+  constexpr bool MIXED = sizeof(R) == 4;
   __shared__ int32_t stk[kNbrWarps][kNodeStack];
   __shared__ int32_t cand[kNbrWarps][64];
   __shared__ R sx[kNbrWarps][XW][32];
   __shared__ R sh[kNbrWarps][32];
+  // staged candidates: nearest-image float position and h^2 widened by the
+  // rounding band (the union mask), then h^2 and the band itself
   __shared__ float4 s4[kNbrWarps][64];
+  __shared__ float2 sb[kNbrWarps][64];
   __shared__ int32_t sj[kNbrWarps][64];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kNbrWarps + wib;
@@ -585,11 +617,21 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
     int sp = 0, nc = 0;
     int ns = 0;  // candidates waiting in the stage (float path)
     const float hi2f = (float)hi * (float)hi;
+    const float tol_i = list_band((float)hi, Lf);
+    const float hi2w = hi2f + tol_i;
+    // the exact predicate for a pair within the rounding band (mixed form)
+    auto exact_pair = [&](int32_t j, bool& g, bool& sc) {
+      const double r2d = exact_r2(xd, n, perm[s], perm[j], Ld);
+      const double hj = (double)hs[j];
+      g = r2d < sq((double)hi);
+      sc = r2d < sq(hj);
+    };
     // float predicate on the nearest images: no per-pair wrap.  The 32
     // staged candidates are tested branch-free into one bit mask of the union
-    // predicate r^2 < max(h_i^2, h_j^2); only the hits (a few per stage) are
-    // then emitted, in candidate order, with the same r^2 recomputed to tell
-    // gather from scatter-only.
+    // predicate r^2 < max(h_i^2, h_j^2), widened by the rounding band; only
+    // the hits (a few per stage) are then emitted, in candidate order, with the
+    // same r^2 recomputed to tell gather from scatter-only and the pairs
+    // within the band decided exactly.
     auto test_stage = [&]() {
       uint32_t hit = 0u;
 #pragma unroll
@@ -597,7 +639,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
         const float4 t = s4[wib][k];
         const float dx = p[0] - t.x, dy = p[1] - t.y, dz = p[2] - t.z;
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        hit |= (r2 < fmaxf(hi2f, t.w) ? 1u : 0u) << k;
+        hit |= (r2 < fmaxf(hi2w, t.w) ? 1u : 0u) << k;
       }
       while (hit) {
         const int k = __ffs(hit) - 1;
@@ -605,10 +647,14 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
         const int32_t j = sj[wib][k];
         if (j == s) continue;
         const float4 t = s4[wib][k];
+        const float2 hb = sb[wib][k];
         const float dx = p[0] - t.x, dy = p[1] - t.y, dz = p[2] - t.z;
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const bool g = r2 < hi2f;
-        const bool sc = r2 < t.w;
+        const int gd = band_decide(r2, hi2f, tol_i);
+        const int sd = band_decide(r2, hb.x, hb.y);
+        bool g = gd == 1, sc = sd == 1;
+        if (gd < 0 || sd < 0) exact_pair(j, g, sc);
+        if (!(g || sc)) continue;
         const uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
         if (kg + ks < cap_pp) {
           const int64_t kk = g ? kg : cap_pp - 1 - ks;
@@ -688,6 +734,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
           // comes out exactly as without the filter.
           int64_t j = -1;
           float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+          float2 tb = make_float2(0.f, 0.f);
           bool pass = false;
           if (kb < take) {
             const int64_t jj = (int64_t)cand[wib][nc + kb] * kBucket + (lane & 7);
@@ -708,7 +755,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
                 }
                 const float Rj = fmaxf(hg, hj) * 1.00001f + 1e-6f * Lf;
                 pass = g2 <= Rj * Rj;
-                t = make_float4(q[0], q[1], q[2], hj * hj);
+                tb = make_float2(hj * hj, list_band(hj, Lf));
+                t = make_float4(q[0], q[1], q[2], tb.x + tb.y);
               }
             }
           }
@@ -716,6 +764,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
           if (pass) {
             const int at = ns + __popc(mp & lt);
             s4[wib][at] = t;
+            sb[wib][at] = tb;
             sj[wib][at] = (int32_t)j;
           }
           ns += __popc(mp);
@@ -725,6 +774,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
             __syncwarp();
             if (lane < ns - 32) {
               s4[wib][lane] = s4[wib][32 + lane];
+              sb[wib][lane] = sb[wib][32 + lane];
               sj[wib][lane] = sj[wib][32 + lane];
             }
             ns -= 32;
@@ -757,8 +807,14 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
               R d[3];
               separation(xi, xj, L, halfL, d);
               const R r2 = norm2(d);
-              const bool g = r2 < hi2;
-              const bool sc = r2 < sq(sh[wib][k]);
+              bool g = r2 < hi2;
+              bool sc = r2 < sq(sh[wib][k]);
+              if constexpr (MIXED) {
+                const float hj = (float)sh[wib][k];
+                const int gd = band_decide((float)r2, hi2f, tol_i);
+                const int sd = band_decide((float)r2, hj * hj, list_band(hj, Lf));
+                if (gd < 0 || sd < 0) exact_pair(j, g, sc);
+              }
               if (!(g || sc)) continue;
               const uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
               if (kg + ks < cap_pp) {
@@ -1028,7 +1084,8 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   uint32_t* ell = reinterpret_cast<uint32_t*>(ws + Ly.ell);
   const unsigned gw = (unsigned)((Ly.nw + kNbrWarps - 1) / kNbrWarps);
   k_nbr<R><<<gw, kNbrWarps * 32, 0, st>>>(k0, xs, hs, boxid, wbox, n, nbk, ni, nt, nrec, p4,
-                                          cnt_g, cnt_s, wlen_g, wlen_s, ell, Ly.cap_pp, hdr);
+                                          cnt_g, cnt_s, wlen_g, wlen_s, ell, Ly.cap_pp, hdr, x,
+                                          perm);
   int32_t* cost = reinterpret_cast<int32_t*>(ws + Ly.item_cost);
   int32_t* seq_cost = reinterpret_cast<int32_t*>(ws + Ly.seq_cost);
   k_balance<<<(unsigned)((n + kBalance - 1) / kBalance), kBalance, 0, st>>>(

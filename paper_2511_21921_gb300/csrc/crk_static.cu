@@ -57,10 +57,23 @@ __global__ void k_static_clear(uint32_t* counts, int64_t ncells) {
   if (c < ncells) counts[c] = 0;
 }
 
+// A particle whose position lies outside [0, L) (or is not finite) gets no
+// cell: it enters no neighbor's sum, and its own volume is NaN.
+__device__ __forceinline__ bool in_box(const double* x, int64_t n, int64_t i, double L) {
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ok = ok && x[a * n + i] >= 0.0 && x[a * n + i] < L;
+  return ok;
+}
+
 __global__ void k_static_count(const double* __restrict__ x, int64_t n, double L, int nc,
                                uint32_t* counts, int32_t* cid) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (!in_box(x, n, i, L)) {
+    cid[i] = -1;
+    return;
+  }
   const int c = (cell_coord(x[i], L, nc) * nc + cell_coord(x[n + i], L, nc)) * nc +
                 cell_coord(x[2 * n + i], L, nc);
   cid[i] = c;
@@ -114,7 +127,7 @@ __global__ void k_static_scatter(const double* __restrict__ x, const R* __restri
                                  int64_t n, const int32_t* __restrict__ cid, uint32_t* cursor,
                                  R* rec) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || cid[i] < 0) return;
   using SR = StaticRec<R>;
   const uint32_t pos = atomicAdd(&cursor[cid[i]], 1u);
   R r[SR::NW];
@@ -136,9 +149,7 @@ __global__ void k_static_volume(const double* __restrict__ x, const R* __restric
   if (i >= n) return;
   using SR = StaticRec<R>;
   const R hi = h[i];
-  bool ok = (double)hi > 0.0 && (double)hi < 0.5 * Ld;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) ok = ok && x[a * n + i] >= 0.0 && x[a * n + i] < Ld;
+  const bool ok = (double)hi > 0.0 && (double)hi < 0.5 * Ld && in_box(x, n, i, Ld);
   if (!ok) {
     V[i] = R(NAN);
     return;
@@ -178,7 +189,9 @@ __global__ void k_static_volume(const double* __restrict__ x, const R* __restric
   V[i] = m[i] / s;
 }
 
-// Scratch address for the current device, looked up once per device.
+// Scratch address for the current device, looked up once per device and kept
+// for the life of the process (a cudaDeviceReset of that device invalidates
+// it; see the header).
 static crk_status static_scratch(unsigned char** out) {
   static std::mutex mu;
   static unsigned char* ptr[128] = {};

@@ -47,29 +47,81 @@ def test_neighbor_sets_bit_exact_fp64(case, mode):
     assert np.array_equal(col, ocol)
 
 
-def test_neighbor_sets_mixed_differ_only_at_the_support_edge():
-    d = synth.load("lognormal32")
+def _csr_vs_oracle(d, precision, mode):
+    """The library's CSR against the oracle's exact predicate on the smoothing
+    lengths the library sees (float32 values in the mixed form)."""
     n = d["h"].shape[0]
-    s = Solver(n, 1, "mixed")
-    t = to_dev(d, "mixed")
+    s = Solver(n, 1, precision)
+    t = to_dev(d, precision)
     s.cell_build(t["x"], t["h"])
-    row, col = (a.cpu().numpy() for a in s.neighbors_csr("gather"))
-    orow, ocol = oracle.neighbors(d["x"], d["h"], 1.0, mode="gather", method="tree")
-    h32 = d["h"].astype(np.float32).astype(np.float64)
-    for i in range(0, n, 37):
-        a = set(col[row[i]:row[i + 1]].tolist())
-        b = set(ocol[orow[i]:orow[i + 1]].tolist()) - {i}
-        for j in a ^ b:
-            dx = d["x"][:, i] - d["x"][:, j]
-            dx -= np.round(dx)
-            r = np.sqrt((dx ** 2).sum())
-            assert abs(r / h32[i] - 1) < 1e-5, (i, j, r, h32[i])
+    assert s.poll() == 0
+    row, col = (a.cpu().numpy() for a in s.neighbors_csr(mode))
+    h = t["h"].double().cpu().numpy()
+    orow, ocol = oracle.neighbors(d["x"], h, d.get("L", 1.0), mode=mode, method="tree")
+    if mode == "gather":
+        keep = ocol != np.repeat(np.arange(n), np.diff(orow))
+        ocol = ocol[keep]
+        orow = np.concatenate([[0], np.cumsum(np.diff(orow) - 1)])
+    return row, col, orow, ocol, s
+
+
+@pytest.mark.parametrize("case", ["lattice16", "multiscale", "lognormal32", "lognormal64"])
+@pytest.mark.parametrize("mode", ["gather", "union"])
+def test_neighbor_sets_bit_exact_mixed(case, mode):
+    """Mixed form: the float candidate test with the exact re-decision inside
+    its rounding band gives the FP64 lists of the same inputs, element for
+    element (the 64^3 box is the benchmark's)."""
+    d = _multiscale() if case == "multiscale" else synth.load(case)
+    row, col, orow, ocol, s = _csr_vs_oracle(d, "mixed", mode)
+    assert np.array_equal(row, orow)
+    assert np.array_equal(col, ocol)
+    if mode == "gather":
+        assert s.stats()["gather_pairs"] == len(ocol)
+
+
+def _dyadic_lattice(n_side, h_pair):
+    """Particles at (i + 1/2)/n_side: every separation, r^2 and h^2 below is a
+    dyadic rational, exact in float and double, so pairs at r = h tie exactly
+    and separations of n_side/2 spacings sit exactly at L/2."""
+    g = np.stack(np.meshgrid(*(np.arange(n_side),) * 3, indexing="ij")).reshape(3, -1)
+    x = (g + 0.5) / n_side
+    N = n_side ** 3
+    h = np.where(g.sum(0) % 2 == 0, h_pair[0], h_pair[1]) / n_side
+    rng = np.random.default_rng(5)
+    return dict(x=x, h=h, m=np.full(N, 1.0 / N), v=rng.normal(0, 0.1, (3, N)),
+                u=np.ones(N), L=1.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [(16, (2.0, 3.0)), (8, (3.0, 2.0))])
+def test_exact_ties_at_the_support_edge(precision, shape):
+    """r = h exactly is outside (strict r < h), on both sides of every pair;
+    separations of exactly L/2 never enter.  16^3 with h = 2 and 3 spacings
+    uses the nearest-image staging of the list build; 8^3 with h up to 3/8 of
+    the box takes the general path.  Both forms equal the oracle and the
+    count of lattice offsets inside the support."""
+    n_side, hp = shape
+    d = _dyadic_lattice(n_side, hp)
+    for mode in ("gather", "union"):
+        row, col, orow, ocol, _ = _csr_vs_oracle(d, precision, mode)
+        assert np.array_equal(row, orow) and np.array_equal(col, ocol), mode
+    # lattice offsets with |o|^2 < (h n)^2 (strict), excluding the origin
+    o = np.arange(-(n_side // 2) + 1, n_side // 2)
+    oo = (o[:, None, None] ** 2 + o[None, :, None] ** 2 + o[None, None, :] ** 2).ravel()
+    row, _, _, _, _ = _csr_vs_oracle(d, precision, "gather")
+    cnt = np.diff(row)
+    even = (np.stack(np.meshgrid(*(np.arange(n_side),) * 3, indexing="ij")).reshape(3, -1)
+            .sum(0) % 2 == 0)
+    assert (cnt[even] == ((oo > 0) & (oo < hp[0] ** 2)).sum()).all()
+    assert (cnt[~even] == ((oo > 0) & (oo < hp[1] ** 2)).sum()).all()
 
 
 # ------------------------------------------------------------------ forward parity
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("case", ["lattice16", "lognormal32"])
+@pytest.mark.parametrize("case", ["lattice16", "lognormal32", "lattice16m", "lognormal32m"])
 def test_forward_parity_whole_box(case, precision):
+    """Every output of the forward path on whole boxes, equal masses and masses
+    spread over 33x (the ``m`` workloads)."""
     d = synth.load(case)
     gpu, s = run_forward(d, precision)
     assert gpu["status"] == 0
@@ -82,8 +134,8 @@ def test_forward_parity_whole_box(case, precision):
     for k, e in err.items():
         assert e < bar, (k, err)
     st = gpu["stats"]
-    if precision == "fp64":  # the float predicate may differ at r = h to rounding
-        assert st["gather_pairs"] == int(ora_pairs(d))
+    h = d["h"].astype(np.float32).astype(np.float64) if precision == "mixed" else d["h"]
+    assert st["gather_pairs"] == int(ora_pairs(dict(d, h=h)))
 
 
 def ora_pairs(d):
@@ -112,8 +164,9 @@ def test_relaxation_partial_flags(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_conservation(precision):
-    d = synth.load("lognormal32")
+@pytest.mark.parametrize("case", ["lognormal32", "lognormal32m"])
+def test_conservation(precision, case):
+    d = synth.load(case)
     gpu, _ = run_forward(d, precision)
     m, v, a, du = d["m"], d["v"], gpu["dvdt"], gpu["dudt"]
     p = np.abs((m * a).sum(1)).max() / np.abs(m * a).sum()
@@ -124,11 +177,12 @@ def test_conservation(precision):
 
 
 # ------------------------------------------------------------------ full size, sampled
-def test_full_size_lognormal64_sampled_mixed():
-    """The benchmark's workload (64^3 lognormal, 100 +- 10 neighbors) in the
-    mixed form and its launch configuration, on outputs the oracle computes one
-    by one."""
-    d = synth.load("lognormal64")
+@pytest.mark.parametrize("case", ["lognormal64", "lognormal64m"])
+def test_full_size_lognormal64_sampled_mixed(case):
+    """The 64^3 clustered workload (lognormal, 100 +- 10 neighbors; equal and
+    unequal masses) in the mixed form, on outputs the oracle computes one by
+    one."""
+    d = synth.load(case)
     gpu, s = run_forward(d, "mixed")
     assert gpu["status"] == 0
     rng = np.random.default_rng(123)
@@ -141,8 +195,9 @@ def test_full_size_lognormal64_sampled_mixed():
         assert e < 5e-5, (k, err)
 
 
-def test_full_size_lognormal64_sampled_fp64():
-    d = synth.load("lognormal64")
+@pytest.mark.parametrize("case", ["lognormal64", "lognormal64m"])
+def test_full_size_lognormal64_sampled_fp64(case):
+    d = synth.load(case)
     gpu, s = run_forward(d, "fp64")
     rng = np.random.default_rng(321)
     tg = np.sort(rng.choice(d["h"].shape[0], 64, replace=False))
