@@ -31,9 +31,20 @@ import numpy as np  # noqa: E402
 
 METRIC = "CRKSPH pair interactions/s (fwd+adjoint step) on 1 GB300"
 UNIT = "pair interactions/s"
-WORKLOAD = "lognormal64"
-WORKLOAD_DESC = ("64^3 = 262,144 gas particles, lognormal density (P(k)~k^-2 field, variance 1.5, "
-                 "seed 1), h for 100+-10 neighbors, u lognormal over 3 decades, periodic unit box")
+# the largest single-GPU configuration (one 256^3 box) is the headline; the
+# clustered 64^3 box is reported beside it
+WORKLOAD = "lognormal256"
+SMALL_WORKLOAD = "lognormal64"
+WORKLOAD_DESCS = {
+    "lognormal256": ("256^3 = 16,777,216 gas particles in one periodic unit box, lognormal "
+                     "density (P(k)~k^-2 field, variance 1.5, seed 5), h for 100+-10 neighbors, "
+                     "u lognormal over 3 decades"),
+    "lognormal64": ("64^3 = 262,144 gas particles, lognormal density (P(k)~k^-2 field, variance "
+                    "1.5, seed 1), h for 100+-10 neighbors, u lognormal over 3 decades, periodic "
+                    "unit box"),
+}
+# boxes above this size are timed on the CPU through a region sample
+REGION_SAMPLE_ABOVE = 1 << 21
 
 # Algorithmic flops per unit of each sweep (add/mul/div/sqrt/exp = 1, fused
 # multiply-add = 2), tallied from the expressions the kernels evaluate.  Units:
@@ -55,9 +66,10 @@ PROFILE_KERNEL = {"b1_volume": "PassB1<float>", "b2_moments": "PassB2<float>",
                   "adj_b1": "PassAB1<float>"}
 
 
-def _profile_of(kernel: str):
-    """(path, metadata, table rows) of the committed ncu summary of ``kernel``,
-    only if it was taken on the current sources (same build digest)."""
+def _profile_of(kernel: str, workload: str, need=None):
+    """(path, metadata, table rows) of the committed ncu summary of ``kernel``
+    on ``workload``, only if it was taken on the current sources (same build
+    digest); ``need`` names a metadata field the summary must carry."""
     import glob
     from paper_2511_21921_gb300 import build as B
     want = PROFILE_KERNEL.get(kernel)
@@ -68,29 +80,32 @@ def _profile_of(kernel: str):
         meta, rows = {}, {}
         with open(path) as fh:
             for line in fh:
-                if ":" in line and line.split(":", 1)[0] in ("kernel", "build_digest",
+                if ":" in line and line.split(":", 1)[0] in ("kernel", "build_digest", "workload",
                                                             "dram_bytes_per_launch"):
                     k, v = line.split(":", 1)
                     meta[k] = v.strip()
                 elif line.startswith("| ") and line.count("|") == 3:
                     k, v = [c.strip() for c in line.strip().strip("|").split("|")]
                     rows[k] = v
-        if want in meta.get("kernel", "") and meta.get("build_digest") == digest:
+        if (want in meta.get("kernel", "") and meta.get("build_digest") == digest and
+                meta.get("workload") == workload and (need is None or need in meta)):
             return path, meta, rows
     return None
 
 
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch of ``kernel`` from a committed ncu summary, only if
-    that summary was taken on the current sources (same build digest)."""
-    p = _profile_of(kernel)
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of ``kernel`` on ``workload`` from a committed ncu
+    summary, only if that summary was taken on the current sources."""
+    p = _profile_of(kernel, workload, need="dram_bytes_per_launch")
     return int(p[1]["dram_bytes_per_launch"]) if p else None
 
 
-def profiled_limiter(kernel: str):
+def profiled_limiter(kernel: str, workload: str):
     """The busiest on-chip unit of ``kernel`` in its committed ncu summary (same
     build digest): L1 throughput, issue activity and FMA-pipe activity, in %."""
-    p = _profile_of(kernel)
+    p = _profile_of(kernel, workload)
+    if p and "L1 throughput, %" not in p[2]:
+        p = None
     if not p:
         return None
     path, _, rows = p
@@ -216,7 +231,10 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- GPU arm
-def run_ours(args, rank, world):
+def run_ours(args, rank, world, workload=None, light=False):
+    """The GPU arm on ``workload`` (default: the command line's).  ``light``
+    times the graph-replayed step and its kernels only (the 64^3 box reported
+    beside the headline)."""
     import torch
     from paper_2511_21921_gb300 import synth
     from paper_2511_21921_gb300 import _lib as L
@@ -225,8 +243,9 @@ def run_ours(args, rank, world):
     from paper_2511_21921_gb300 import dist as D
     dev = torch.device("cuda", _env_int("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
+    name = workload or args.workload
     # independent boxes are sharded whole across ranks; one box is replicated
-    d = D.shard_workload(synth.load(args.workload), rank, world)
+    d = D.shard_workload(synth.load(name), rank, world)
     n = d["h"].shape[0]
     prec = args.precision
     dt = torch.float32 if prec == "mixed" else torch.float64
@@ -311,6 +330,49 @@ def run_ours(args, rank, world):
     step_ms = D.max_over_ranks(sum(ms) / len(ms), device=dev)
     job_pairs = D.sum_over_ranks(pairs, device=dev)
     status = s.poll()
+
+    def kernel_times(nk):
+        """Mean per-launch milliseconds of every library phase over ``nk`` steps
+        (library CUDA events on the launching stream)."""
+        L.crk_timing_enable(s.plan, True)
+        kt = {}
+        for k in range(nk):
+            flush.fill_(k & 0xff)
+            step(dv)
+            for nm, t in L.crk_timing_read(s.plan):
+                kt.setdefault(nm, []).append(t)
+        L.crk_timing_enable(s.plan, False)
+        return {k: sum(v) / len(v) for k, v in kt.items()}
+
+    def roofline_of(kmean, alu_fp32=None):
+        units = {"gather": pairs, "union": upairs}
+        dom = max((k for k in kmean if k in FLOPS_PER_PAIR), key=lambda k: kmean[k])
+        achieved = FLOPS_PER_PAIR[dom] * units[UNIT_OF[dom]] / (kmean[dom] * 1e-3) / 1e12
+        per_kernel = {k: round(FLOPS_PER_PAIR[k] * units[UNIT_OF[k]] / (kmean[k] * 1e-3) / 1e12, 3)
+                      for k in kmean if k in FLOPS_PER_PAIR}
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
+                "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "traffic": profiled_traffic(dom, name),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "flops_per_pair": FLOPS_PER_PAIR[dom], "pairs": units[UNIT_OF[dom]],
+                "kernel_ms": round(kmean[dom], 4),
+                "frac_of_measured_fp32": round(achieved / alu_fp32, 4) if alu_fp32 else None,
+                "on_chip": profiled_limiter(dom, name)}
+        return roof, per_kernel
+
+    if light:
+        kmean = kernel_times(max(3, min(args.steps, 20)))
+        roof, per_kernel = roofline_of(kmean)
+        return {"workload": WORKLOAD_DESCS.get(name, name), "name": name, "n": n,
+                "gather_pairs": pairs, "union_pairs": upairs,
+                "value": job_pairs / (step_ms * 1e-3), "unit": UNIT,
+                "ms_per_step": round(step_ms, 4), "steps": args.steps,
+                "ms_per_step_median": round(float(np.median(ms)), 4),
+                "roofline": roof, "kernel_ms": {k: round(v, 4) for k, v in sorted(kmean.items())},
+                "kernel_tflops": per_kernel, "gpu_launches": launches, "clocks": clocks,
+                "autotune": {k: v["variant"] for k, v in tuned.items()} if tuned else None,
+                "device_status": status}, pairs
 
     # end to end: pinned host inputs -> device, step, results -> pinned host
     out_h = (torch.empty((3, n), dtype=dt).pin_memory(), torch.empty(n, dtype=dt).pin_memory())
@@ -449,40 +511,17 @@ def run_ours(args, rank, world):
                         " over the lists of the last build"}
 
     # per-kernel durations (library CUDA events on the launching stream)
-    L.crk_timing_enable(s.plan, True)
-    kt = {}
-    nk = max(3, min(args.steps, 20))
-    for k in range(nk):
-        flush.fill_(k & 0xff)
-        step(dv)
-        for name, t in L.crk_timing_read(s.plan):
-            kt.setdefault(name, []).append(t)
-    L.crk_timing_enable(s.plan, False)
-    kmean = {k: sum(v) / len(v) for k, v in kt.items()}
+    kmean = kernel_times(max(3, min(args.steps, 20)))
     fwd_names = ("build.check", "build.keys_sort", "build.tree", "build.lists", "pack_b1",
                  "b1_volume", "b2_moments", "pack_c1", "c1_density", "c2_rates")
     fwd_ms = sum(kmean.get(k, 0.0) for k in fwd_names)
-    units = {"gather": pairs, "union": upairs}
-    dom = max((k for k in kmean if k in FLOPS_PER_PAIR), key=lambda k: kmean[k])
-    flops = FLOPS_PER_PAIR[dom] * units[UNIT_OF[dom]]
-    achieved = flops / (kmean[dom] * 1e-3) / 1e12
-    per_kernel_tflops = {k: round(FLOPS_PER_PAIR[k] * units[UNIT_OF[k]] / (kmean[k] * 1e-3) / 1e12, 3)
-                         for k in kmean if k in FLOPS_PER_PAIR}
     # measured FMA-chain rates (same clocks and power state as the sweeps)
     f32, _ = L.crk_alu_peak(stream.cuda_stream, False, 16384)
     f64, _ = L.crk_alu_peak(stream.cuda_stream, True, 512)
     alu_peak = {"fp32_tflops": round(f32 / 1e12, 3), "fp64_tflops": round(f64 / 1e12, 4),
                 "fp32_over_fp64": round(f32 / f64, 1) if f64 > 0 else None,
                 "method": "FMA chains, 8 per thread, 8 x 256 threads per SM, best of 3"}
-    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
-                "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": profiled_traffic(dom),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                "flops_per_pair": FLOPS_PER_PAIR[dom], "pairs": units[UNIT_OF[dom]],
-                "kernel_ms": round(kmean[dom], 4),
-                "frac_of_measured_fp32": round(achieved / alu_peak["fp32_tflops"], 4)
-                if alu_peak["fp32_tflops"] > 0 else None,
-                "on_chip": profiled_limiter(dom)}
+    roofline, per_kernel_tflops = roofline_of(kmean, alu_peak["fp32_tflops"])
     res = {
         "metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
@@ -490,8 +529,8 @@ def run_ours(args, rank, world):
         "value": job_pairs / (step_ms * 1e-3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload,
-                   "name": args.workload, "n": n, "boxes": nb,
+        "config": {"workload": WORKLOAD_DESCS.get(name, name),
+                   "name": name, "n": n, "boxes": nb,
                    "gather_pairs": pairs, "union_pairs": upairs,
                    "precision": prec, "step": "build+moments+rates" + ("+adjoint" if with_adj
                                                                        else ""),
@@ -518,11 +557,14 @@ def run_ours(args, rank, world):
         "clocks": clocks,
         "device_status": status,
     }
-    if args.hydro and world == 1 and "box_off" not in d:
-        res["hydro_step"] = hydro_step(args, d, dev, flush)
-        res["cooling"] = cooling_leg(args, d, dev, flush)
-        res["subgrid"] = subgrid_leg(args, d, dev, flush)
-        res["active_set"] = active_leg(args, d, dev, flush)
+    if args.hydro and world == 1:
+        # the other rows of the path, on the clustered 64^3 box
+        ds = synth.load(SMALL_WORKLOAD)
+        res["other_rows_workload"] = SMALL_WORKLOAD
+        res["hydro_step"] = hydro_step(args, ds, dev, flush)
+        res["cooling"] = cooling_leg(args, ds, dev, flush)
+        res["subgrid"] = subgrid_leg(args, ds, dev, flush)
+        res["active_set"] = active_leg(args, ds, dev, flush)
     if args.fp64_compare and world == 1 and prec == "mixed":
         res["fp64_gpu"] = fp64_compare(args, d, dev)
         if res["fp64_gpu"]:
@@ -771,10 +813,11 @@ def fp64_compare(args, d, dev):
         if not args.fwd_only:
             s.adjoint(t64["v"], t64["u"], t64["ga"], t64["gu"], recompute=False)
 
-    for _ in range(2):
+    big = n > REGION_SAMPLE_ABOVE  # a step of the FP64 form takes seconds there
+    for _ in range(1 if big else 2):
         step()
     torch.cuda.synchronize()
-    k = max(2, min(5, args.steps))
+    k = 2 if big else max(2, min(5, args.steps))
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(k):
@@ -782,7 +825,8 @@ def fp64_compare(args, d, dev):
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / k
-    return {"ms_per_step": round(ms, 4), "value": s.stats()["gather_pairs"] / (ms * 1e-3)}
+    return {"ms_per_step": round(ms, 4), "value": s.stats()["gather_pairs"] / (ms * 1e-3),
+            "steps": k}
 
 
 # ---------------------------------------------------------------------------- CPU arm
@@ -795,63 +839,70 @@ def _cores():
 
 def oracle_pass(d, with_derivative=True):
     """One oracle evaluation of the step: forward values and, for the adjoint
-    part, the oracle's derivative pass (forward-mode JVP; it has no reverse)."""
+    part, the oracle's derivative pass (forward-mode JVP; it has no reverse).
+    Returns (seconds, gather pairs per particle)."""
     import oracle
     n = d["h"].shape[0]
     t0 = time.perf_counter()
     if with_derivative:
         rng = np.random.default_rng(0)
-        oracle.jvp(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], tx=rng.normal(size=(3, n)) * 1e-4,
-                   want=("dvdt", "dudt"))
+        o, _ = oracle.jvp(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"],
+                          tx=rng.normal(size=(3, n)) * 1e-4, want=("dvdt", "dudt", "kgather"))
     else:
-        oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], want=("dvdt", "dudt"))
-    return time.perf_counter() - t0
+        o = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"],
+                           want=("dvdt", "dudt", "kgather"))
+    return time.perf_counter() - t0, o["kgather"]
 
 
-def _oracle_pairs(d):
-    import oracle
-    o = oracle.forward(d["x"], d["h"], d["m"], L=d["L"], want=("kgather",))
-    return int(o["kgather"].sum())
-
-
-def cpu_baseline(args, min_seconds=10.0, max_passes=20):
-    """The oracle as it stands on the host cores: passes over the whole
-    benchmark workload (each one forward-mode pass with one JVP), repeated
-    until about ten seconds of wall time have been spent."""
+def cpu_sample(name, side):
+    """The oracle's input for a bounded sample of workload ``name``: the whole
+    box when it is small, otherwise a cube of ``side`` (box units) at the box
+    center with the particles its results depend on (synth.region_sample).
+    Returns (input, owned mask, description)."""
     from paper_2511_21921_gb300 import synth
+    d = synth.load(name)
+    n = d["h"].shape[0]
+    if n <= REGION_SAMPLE_ABOVE:
+        return d, np.ones(n, dtype=bool), f"whole {name} workload"
+    sub, own, _ = synth.region_sample(d, side)
+    desc = (f"region of {name}: the {int(own.sum())} particles of a cube of side {side} at the "
+            f"box center (owned) plus the {int((~own).sum())} within three times the largest "
+            "smoothing length of them (ghosts, which the owned particles' rates depend on); "
+            "the owned particles' results equal the whole box's; pairs counted = the owned "
+            "particles' gather pairs")
+    return sub, own, desc
+
+
+def cpu_baseline(args, min_seconds=10.0, max_passes=20, side=0.3):
+    """The oracle as it stands on the host cores: passes over a bounded sample of
+    the benchmark workload (each one forward-mode pass with one JVP), repeated
+    until about ten seconds of wall time have been spent."""
     import oracle
-    d = synth.load(args.workload)
-    pairs = _oracle_pairs(d)
-    t, k = 0.0, 0
+    d, own, desc = cpu_sample(args.workload, side)
+    t, k, pairs = 0.0, 0, 0
     while k < max_passes and (k == 0 or t < min_seconds):
-        t += oracle_pass(d, not args.fwd_only)
+        dt_, kg = oracle_pass(d, not args.fwd_only)
+        t += dt_
+        pairs = int(kg[own].sum())
         k += 1
     return {"value": k * pairs / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"whole {args.workload} workload ({pairs} gather pairs) x {k} passes, each "
-                      "one oracle forward pass with one forward-mode derivative (JVP), FP64, "
-                      "OpenMP over particles",
+            "sample": f"{desc} ({pairs} pairs) x {k} passes, each one oracle forward pass with "
+                      "one forward-mode derivative (JVP), FP64, OpenMP over particles",
             "seconds": round(t, 3)}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle timed step by step on the host cores."""
-    from paper_2511_21921_gb300 import synth
+    """Reference arm: the FP64 CPU oracle timed step by step on the host cores,
+    each step one oracle pass over a bounded sample of the workload."""
     import oracle
     oracle.build()
-    budget = 150.0 / max(1, args.steps + args.warmup)  # seconds per step
-    name = args.workload
-    d = synth.load(name)
-    probe = oracle_pass(d, not args.fwd_only)
-    sample = f"whole {name} workload"
-    if probe > budget and name == "lognormal64":
-        name = "lognormal32"  # same generator and statistics, 1/8 of the particles
-        d = synth.load(name)
-        sample = ("lognormal32: same generator and statistics as lognormal64, 1/8 of the "
-                  "particles (per-step budget)")
-    pairs = _oracle_pairs(d)
-    for _ in range(args.warmup):
+    side = 0.2
+    d, own, sample = cpu_sample(args.workload, side)
+    _, kg = oracle_pass(d, not args.fwd_only)  # also warms the oracle
+    pairs = int(kg[own].sum())
+    for _ in range(max(0, args.warmup - 1)):
         oracle_pass(d, not args.fwd_only)
-    ts = [oracle_pass(d, not args.fwd_only) for _ in range(args.steps)]
+    ts = [oracle_pass(d, not args.fwd_only)[0] for _ in range(args.steps)]
     mean = sum(ts) / len(ts)
     val = pairs / mean
     cores = oracle.num_threads()
@@ -860,8 +911,8 @@ def run_reference(args):
         "higher_is_better": True, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(mean * 1e3, 3), "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "name": args.workload, "sample": sample,
-                   "gather_pairs_per_step": pairs},
+        "config": {"workload": WORKLOAD_DESCS.get(args.workload, args.workload),
+                   "name": args.workload, "sample": sample, "gather_pairs_per_step": pairs},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample + "; forward values plus one JVP per step"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -872,7 +923,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -882,6 +933,8 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false", default=True)
     ap.add_argument("--prefetch", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-small", dest="small", action="store_false", default=True,
+                    help="skip the 64^3 box reported beside the headline")
     ap.add_argument("--no-hydro", dest="hydro", action="store_false", default=True)
     ap.add_argument("--fp64-compare", action="store_true", default=True)
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
@@ -899,6 +952,8 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     res, _ = run_ours(args, rank, world)
+    if args.small and world == 1 and args.workload != SMALL_WORKLOAD:
+        res[SMALL_WORKLOAD], _ = run_ours(args, rank, world, workload=SMALL_WORKLOAD, light=True)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             res["cpu_baseline"] = cpu_baseline(args)

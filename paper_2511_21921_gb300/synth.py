@@ -195,6 +195,39 @@ def cotangents(n, seed=4):
     return rng.standard_normal((3, n)), rng.standard_normal(n)
 
 
+def region_sample(d, side, center=0.5, hops=3):
+    """A cubic region of box ``d`` with the particles its results depend on.
+
+    Owned particles lie within ``side``/2 of ``center`` on every axis (no
+    periodic wrap, so the cube must sit inside the box).  The sample adds every
+    particle within a margin of ``hops`` times the largest smoothing length of
+    the sample, grown until it stops changing: a particle's rates depend only
+    on particles within three neighbor hops, and a hop is shorter than the
+    larger smoothing length of the pair.  Particles keep their relative order,
+    so neighbor lists sorted by index are sorted the same way in the sample.
+    Returns the sample (same keys as ``d``), the boolean mask of its owned
+    particles and the indices of the sample's particles in ``d``.
+    """
+    x, h = d["x"], d["h"]
+    off = np.abs(x - center)
+    own = np.all(off < 0.5 * side, axis=0)
+    margin = hops * float(h[own].max())
+    while True:
+        reg = np.all(off < 0.5 * side + margin, axis=0)
+        m2 = hops * float(h[reg].max())
+        if m2 <= margin:
+            break
+        margin = m2
+    if 0.5 * side + margin >= min(center, d["L"] - center):
+        raise ValueError("region with its margin does not fit inside the box")
+    idx = np.nonzero(reg)[0]
+    out = {k: (d[k][..., idx] if k in ("x", "v", "u", "h", "m") else d[k]) for k in d
+           if k not in ("box_off", "box_L", "sides", "sigma2")}
+    out["x"] = np.ascontiguousarray(out["x"])
+    out["v"] = np.ascontiguousarray(out["v"])
+    return out, own[idx], idx
+
+
 def unequal_masses(d, seed=6, sigma=0.7, cut=2.5):
     """A copy of workload ``d`` whose masses are lognormal: ln(m N) ~ N(0, sigma)
     truncated at ``cut`` sigma (a spread of exp(2 cut sigma) = 33x for the
