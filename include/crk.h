@@ -98,14 +98,22 @@ typedef struct {
   int32_t blocks_per_sm; /* resident blocks per SM for the persistent sweeps; 0 = default */
   int32_t prefetch;      /* sweeps prefetch the neighbor record this many list entries ahead
                             into L1; 0 = off */
-  int32_t reserved[2];
+  int32_t energy_split;  /* compatible energy split of the pair work E_ij = m_i a_ij.(v_j - v_i)
+                            (Sec. 2.1): 0 = halves, f_ij = 1/2; 1 = weighted by the specific
+                            energies, f_ij = (1 + sgn(E_ij)(u_j - u_i)/(u_i + u_j))/2, so heating
+                            goes mostly to the colder particle and cooling is drawn mostly from
+                            the hotter one; f_ij + f_ji = 1 either way */
+  int32_t q_side;        /* viscosity in the momentum rate: 0 = (P_i + P_j + Q_ij + Q_ji) with
+                            (G_ij - G_ji); 1 = per side, (P_i + P_j)(G_ij - G_ji) +
+                            2 (Q_ij G_ij - Q_ji G_ji), each Q with its own side's gradient */
 } crk_params;
 
 typedef struct crk_plan crk_plan;
 
 /* Fill `p` with the library defaults: gamma = 5/3, Cl = 2, Cq = 1, eps2 = 0.01,
  * eta_crit = 1/n_h for n_h = (3*100/(4 pi))^(1/3), eta_fold = 0.2, relaxation
- * off, limiter on, CRK_MIXED32.  Host only. */
+ * off, limiter on, energy halves, viscosity with the pressures, CRK_MIXED32.
+ * Host only. */
 void crk_params_default(crk_params* p);
 
 /* Create a plan for up to n_max particles in up to n_boxes_max boxes.  The plan

@@ -260,6 +260,8 @@ typedef struct {
   double eta_fold;  // near-field damping width
   double relax_dt;  // relaxation time step; 0 turns relaxation off (App. A.1)
   int32_t limiter;  // 1: limited viscosity, 0: unlimited
+  int32_t energy_split;  // 0: f_ij = 1/2; 1: weighted by the specific energies
+  int32_t q_side;   // 0: Q_ij + Q_ji with the pressures; 1: each Q with its own gradient
   int32_t pad;
 } oracle_params;
 
@@ -558,7 +560,16 @@ struct Eval {
   //   G_ij = grad W^R_ij (i's coefficients, h_i); G_ji likewise with j's and x_ji
   //   limited viscosity Q_ij, Q_ji; Pi = P_i + P_j + Q_ij + Q_ji
   //   m_i a_ij = -(1/2) V_i V_j Pi (G_ij - G_ji)
-  //   dv_i/dt = sum_j a_ij;  du_i/dt = (1/m_i) sum_j (1/2) m_i a_ij . (v_j - v_i)
+  //   or, with q_side, each side's viscosity with its own gradient:
+  //   m_i a_ij = -(1/2) V_i V_j [(P_i + P_j)(G_ij - G_ji) + 2 (Q_ij G_ij - Q_ji G_ji)]
+  //   (both antisymmetric in i, j; equal when Q_ij = Q_ji)
+  //   pair work E_ij = m_i a_ij . (v_j - v_i) (symmetric in i, j)
+  //   dv_i/dt = sum_j a_ij;  du_i/dt = (1/m_i) sum_j f_ij E_ij
+  //   compatible split (Sec. 2.1): f_ij + f_ji = 1, so the pair's thermal energy
+  //   change is its kinetic energy loss.  f_ij = 1/2, or with energy_split
+  //   f_ij = (1/2)(1 + sgn(E_ij) (u_j - u_i)/(u_i + u_j)): heating goes mostly
+  //   to the particle with the lower specific energy, cooling is drawn mostly
+  //   from the one with the higher (1/2 when u_i + u_j = 0 or E_ij = 0).
   void calcRates(int64_t i, T dv[3], T& du) {
     ensureRho(i);
     const auto& nb = unionset(i);
@@ -603,13 +614,26 @@ struct Eval {
       T muj = tmin(T(0.0), dot3(vhat, etaj) / (dot3(etaj, etaj) + T(p.eps2)));
       T Qi = rho[i] * (T(0.0) - T(p.Cl) * cs[i] * mui + T(p.Cq) * mui * mui);
       T Qj = rho[j] * (T(0.0) - T(p.Cl) * cs[j] * muj + T(p.Cq) * muj * muj);
-      T Pi = P[i] + P[j] + Qi + Qj;
-      T pre = T(-0.5) * V[i] * V[j] * Pi;
       T F[3];
-      for (int a = 0; a < 3; ++a) F[a] = pre * (Gi[a] - Gj[a]);
+      if (p.q_side) {
+        T VV = T(-0.5) * V[i] * V[j];
+        T PP = P[i] + P[j];
+        for (int a = 0; a < 3; ++a)
+          F[a] = VV * (PP * (Gi[a] - Gj[a]) + T(2.0) * (Qi * Gi[a] - Qj * Gj[a]));
+      } else {
+        T Pi = P[i] + P[j] + Qi + Qj;
+        T pre = T(-0.5) * V[i] * V[j] * Pi;
+        for (int a = 0; a < 3; ++a) F[a] = pre * (Gi[a] - Gj[a]);
+      }
       for (int a = 0; a < 3; ++a) acc[a] += F[a] / m[i];
       T w = F[0] * (v[0][j] - v[0][i]) + F[1] * (v[1][j] - v[1][i]) + F[2] * (v[2][j] - v[2][i]);
-      eacc += T(0.5) * w;
+      T f(0.5);
+      if (p.energy_split) {
+        double su = val(u[i]) + val(u[j]);
+        double sg = val(w) > 0 ? 1.0 : (val(w) < 0 ? -1.0 : 0.0);
+        if (su > 0 && sg != 0) f = T(0.5) * (T(1.0) + T(sg) * (u[j] - u[i]) / (u[i] + u[j]));
+      }
+      eacc += f * w;
     }
     for (int a = 0; a < 3; ++a) dv[a] = acc[a];
     du = eacc / m[i];

@@ -54,14 +54,15 @@ def build(force: bool = False) -> str:
 class OracleParams(C.Structure):
     _fields_ = [("gamma", C.c_double), ("Cl", C.c_double), ("Cq", C.c_double),
                 ("eps2", C.c_double), ("eta_crit", C.c_double), ("eta_fold", C.c_double),
-                ("relax_dt", C.c_double), ("limiter", C.c_int32), ("pad", C.c_int32)]
+                ("relax_dt", C.c_double), ("limiter", C.c_int32), ("energy_split", C.c_int32),
+                ("q_side", C.c_int32), ("pad", C.c_int32)]
 
 
 def default_params(**kw) -> OracleParams:
     """The reading of the viscosity constants used throughout (configurable)."""
     n_h = (3.0 * 100 / (4.0 * np.pi)) ** (1.0 / 3.0)
     d = dict(gamma=5.0 / 3.0, Cl=2.0, Cq=1.0, eps2=0.01, eta_crit=1.0 / n_h,
-             eta_fold=0.2, relax_dt=0.0, limiter=1)
+             eta_fold=0.2, relax_dt=0.0, limiter=1, energy_split=0, q_side=0)
     d.update(kw)
     return OracleParams(**d, pad=0)
 

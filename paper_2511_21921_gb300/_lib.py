@@ -27,7 +27,7 @@ class crk_params(C.Structure):
                 ("relax_dt", C.c_double), ("limiter", C.c_int32), ("precision", C.c_int32),
                 ("nbr_cap", C.c_int32), ("block_threads", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("prefetch", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("energy_split", C.c_int32), ("q_side", C.c_int32)]
 
 
 class crk_stats(C.Structure):

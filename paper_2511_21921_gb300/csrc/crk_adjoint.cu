@@ -11,6 +11,8 @@
 // its own outputs (gather flag) and its contribution to the neighbor's outputs
 // (scatter flag) -- so no atomics and no per-pair storage are needed.  Neighbor
 // sets, image shifts, relaxation flags and limiter branches are held fixed.
+#include <cstring>
+
 #include "crk_sweep.cuh"
 
 namespace crk {
@@ -216,10 +218,15 @@ __global__ void k_adj_prep(const R* __restrict__ gdv, const R* __restrict__ gdu,
 
 // ===========================================================================
 // c2^T: reverse of the pair rates.  For the unordered pair {i, j},
-//   L_ij = F.(alpha_i - alpha_j) - (beta_i + beta_j) F.(v_i - v_j)
-// and thread i takes the derivative with respect to its own variables.
+//   L_ij = F.(alpha_i - alpha_j) + 2 (beta_i f_ij + beta_j f_ji) E_ij,
+//   E_ij = F.(v_j - v_i)   (f = 1/2 unless the energy split is on)
+// and thread i takes the derivative with respect to its own variables (the
+// share's u_i dependence included; the sign of E_ij is held, as every branch).
 // ===========================================================================
-template <class R> struct PassA2 {
+template <class R, bool VAR = false> struct PassA2 {
+  // VAR: the formulation variants (per-side viscosity, energy split) are
+  // compiled in; the default form is compiled without them so that its
+  // register allocation is not affected.
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 5, MB2 = 6;  // resident-block variants
@@ -254,6 +261,7 @@ template <class R> struct PassA2 {
     R L, halfL, rho, cs;
     int64_t s;
     R xb[3], vb[3], hb, Vb, Pb, rhob, cb;
+    R u, ubs;  // specific energy and its cotangent through the energy split
     R Cb[16], gvb[9];
     R fa[3];
     Acc<R> fe;
@@ -270,6 +278,8 @@ template <class R> struct PassA2 {
 #pragma unroll
     for (int k = 0; k < 3; ++k) st.xb[k] = st.vb[k] = R(0);
     st.hb = st.Vb = st.Pb = st.rhob = st.cb = R(0);
+    st.u = VAR ? a.us[s] : R(0);
+    st.ubs = R(0);
 #pragma unroll
     for (int k = 0; k < 16; ++k) st.Cb[k] = R(0);
 #pragma unroll
@@ -336,43 +346,85 @@ template <class R> struct PassA2 {
     const R qai = ri[RC::C2_QA], qbi = ri[RC::C2_QB], qaj = rj[RC::C2_QA], qbj = rj[RC::C2_QB];
     const R Qi = mui * (qbi * mui - qai);
     const R Qj = muj * (qbj * muj - qaj);
-    const R Pi = (ri[RC::C2_P] + rj[RC::C2_P]) + (Qi + Qj);
     const R ViVj = ri[RC::C2_V] * rj[RC::C2_V];
-    const R pre = R(-0.5) * ViVj * Pi;
+    const bool qside = VAR && a.av.q_side;
+    R Pi = R(0), pre = R(0), VV = R(0), PP = R(0);
     R F[3], dG[3];
+    if (qside) {  // the expressions of PairC2::force, per-side viscosity
+      VV = R(-0.5) * ViVj;
+      PP = ri[RC::C2_P] + rj[RC::C2_P];
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      dG[p] = Gi[p] - Gj[p];
-      F[p] = pre * dG[p];
+      for (int p = 0; p < 3; ++p) {
+        dG[p] = Gi[p] - Gj[p];
+        const R qg = rsub(rmul(Qi, Gi[p]), rmul(Qj, Gj[p]));
+        F[p] = VV * radd(rmul(PP, dG[p]), R(2) * qg);
+      }
+    } else {
+      Pi = (ri[RC::C2_P] + rj[RC::C2_P]) + (Qi + Qj);
+      pre = R(-0.5) * ViVj * Pi;
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        dG[p] = Gi[p] - Gj[p];
+        F[p] = pre * dG[p];
+      }
+    }
+    // pair work E_ij = F.(v_j - v_i) and i's share f_ij of it
+    const R E = -(F[0] * vij[0] + F[1] * vij[1] + F[2] * vij[2]);
+    R f = R(0.5), dfdui = R(0);
+    if (VAR && a.av.energy_split) {
+      const R uj = a.us[j];
+      f = energy_share(true, E, st.u, uj);
+      const R su = st.u + uj;
+      if (su > R(0) && E != R(0)) dfdui = (E > R(0) ? -uj : uj) / (su * su);
     }
     if (a.dvdt) {  // forward rates from the same force (fused sweep)
 #pragma unroll
       for (int p = 0; p < 3; ++p) st.fa[p] += F[p];
-      st.fe.add(R(-0.5) * (F[0] * vij[0] + F[1] * vij[1] + F[2] * vij[2]));
+      st.fe.add(f * E);
     }
-    // ---- reverse
-    const R bsum = st.ab[3] + abj[3];
+    // ---- reverse.  beta = g_dudt / (2 m), so the energy term of the pair is
+    // c E with c = 2 (beta_i f_ij + beta_j f_ji) (beta_i + beta_j for halves)
+    const R csum = R(2) * (st.ab[3] * f + abj[3] * (R(1) - f));
+    if (VAR && a.av.energy_split) st.ubs += R(2) * (st.ab[3] - abj[3]) * E * dfdui;
     R Fb[3], vijb[3];
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
-      Fb[p] = (st.ab[p] - abj[p]) - bsum * vij[p];
-      vijb[p] = -bsum * F[p];
+      Fb[p] = (st.ab[p] - abj[p]) - csum * vij[p];
+      vijb[p] = -csum * F[p];
     }
-    const R preb = Fb[0] * dG[0] + Fb[1] * dG[1] + Fb[2] * dG[2];
-    R Gib[3], Gjb[3];
+    R Gib[3], Gjb[3], Qib, Qjb;
+    if (qside) {
+      // F = VV [PP dG + 2 (Q_i G_i - Q_j G_j)]
+      R VVb = R(0), FdG = R(0), FGi = R(0), FGj = R(0);
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      Gib[p] = pre * Fb[p];
-      Gjb[p] = -Gib[p];
+      for (int p = 0; p < 3; ++p) {
+        VVb += Fb[p] * (PP * dG[p] + R(2) * (Qi * Gi[p] - Qj * Gj[p]));
+        FdG += Fb[p] * dG[p];
+        FGi += Fb[p] * Gi[p];
+        FGj += Fb[p] * Gj[p];
+        Gib[p] = VV * (PP + R(2) * Qi) * Fb[p];
+        Gjb[p] = -VV * (PP + R(2) * Qj) * Fb[p];
+      }
+      Qib = R(2) * VV * FGi;
+      Qjb = R(-2) * VV * FGj;
+      st.Vb += VVb * (R(-0.5) * rj[RC::C2_V]);
+      st.Pb += VV * FdG;
+    } else {
+      const R preb = Fb[0] * dG[0] + Fb[1] * dG[1] + Fb[2] * dG[2];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        Gib[p] = pre * Fb[p];
+        Gjb[p] = -Gib[p];
+      }
+      const R Pib = preb * (R(-0.5) * ViVj);
+      st.Vb += preb * (R(-0.5) * rj[RC::C2_V] * Pi);
+      st.Pb += Pib;
+      Qib = Qjb = Pib;
     }
-    const R Pib = preb * (R(-0.5) * ViVj);
-    st.Vb += preb * (R(-0.5) * rj[RC::C2_V] * Pi);
-    st.Pb += Pib;
-    const R Qb = Pib;
-    const R muib = Qb * (R(2) * qbi * mui - qai);
-    const R mujb = Qb * (R(2) * qbj * muj - qaj);
-    st.rhob += Qb * mui * (a.Cq * mui - a.Cl * st.cs);
-    st.cb += Qb * mui * (-a.Cl * st.rho);
+    const R muib = Qib * (R(2) * qbi * mui - qai);
+    const R mujb = Qjb * (R(2) * qbj * muj - qaj);
+    st.rhob += Qib * mui * (a.Cq * mui - a.Cl * st.cs);
+    st.cb += Qib * mui * (-a.Cl * st.rho);
     R vxb = R(0), r2b = R(0), ihib = R(0), rb = R(0);
     R db[3] = {R(0), R(0), R(0)};
     if (tmi < R(0)) {
@@ -459,7 +511,8 @@ template <class R> struct PassA2 {
     const R u = a.us[s];
     // EOS: P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u)
     const R rhob = st.rhob + a.gm1 * u * st.Pb;
-    const R ub = a.gm1 * st.rho * st.Pb + (st.cs > R(0) ? st.cb * a.ggm1 / (R(2) * st.cs) : R(0));
+    const R ub = a.gm1 * st.rho * st.Pb + (st.cs > R(0) ? st.cb * a.ggm1 / (R(2) * st.cs) : R(0)) +
+                 st.ubs;
     // rho = N / D
     const R D = a.Ds[s];
     const R Nb = rhob / D, Db = -rhob * st.rho / D;
@@ -932,7 +985,14 @@ crk_status adjoint_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const
                               (R)(p.gamma * (p.gamma - 1.0)),
                               dvdt,
                               dudt};
-  launch_sweep<PassA2<R>>(plan, st, a2, dvdt ? "rates_adj_c2" : "adj_c2");
+  if (p.q_side || p.energy_split) {
+    typename PassA2<R, true>::Args av2;
+    static_assert(sizeof(av2) == sizeof(a2), "same arguments");
+    memcpy(&av2, &a2, sizeof(a2));
+    launch_sweep_plain<PassA2<R, true>>(plan, st, av2, dvdt ? "rates_adj_c2" : "adj_c2");
+  } else {
+    launch_sweep<PassA2<R>>(plan, st, a2, dvdt ? "rates_adj_c2" : "adj_c2");
+  }
   typename PassA1<R>::Args a1{c, rec_a1, reinterpret_cast<const R*>(ws + Ly.mom), cbar, rec_a2,
                               acc};
   launch_sweep<PassA1<R>>(plan, st, a1, "adj_c1");

@@ -116,6 +116,8 @@ static bool params_ok(const crk_params& p) {
   if (p.block_threads != 0 && (p.block_threads % 32 != 0 || p.block_threads > 256)) return false;
   if (p.blocks_per_sm < 0 || p.blocks_per_sm > 64) return false;
   if (p.prefetch < 0 || p.prefetch > 16) return false;
+  if ((p.energy_split != 0 && p.energy_split != 1) || (p.q_side != 0 && p.q_side != 1))
+    return false;
   return true;
 }
 

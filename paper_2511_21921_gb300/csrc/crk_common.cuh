@@ -219,6 +219,16 @@ __device__ __forceinline__ void separation(const float* xi, const float* xj, flo
   }
 }
 
+// products, sums and differences rounded on their own (no contraction into a
+// fused multiply-add), for expressions whose two sides of a pair must come out
+// as exact negations of each other
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+
 template <class R> __device__ __forceinline__ R rsqrt_(R x);
 template <> __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 template <> __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }

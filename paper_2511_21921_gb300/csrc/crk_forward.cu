@@ -3,6 +3,8 @@
 // takes 32 consecutive sorted particles from an atomic work queue, each lane
 // walks its own neighbor list (gather or union part) and gathers the
 // neighbor's packed record from global memory.
+#include <cstring>
+
 #include "crk_sweep.cuh"
 
 namespace crk {
@@ -352,11 +354,15 @@ template <class R> struct PassC1 {
 // ===========================================================================
 // c2: pair rates over U(i) with the limited artificial viscosity
 //   Pi = P_i + P_j + Q_ij + Q_ji,   F_ij = -(1/2) V_i V_j Pi (G_ij - G_ji)
-//   dv_i/dt = sum F_ij / m_i,  du_i/dt = sum (1/2) F_ij.(v_j - v_i) / m_i
+//   (or the per-side viscosity, see PairC2::force)
+//   dv_i/dt = sum F_ij / m_i,  du_i/dt = sum f_ij F_ij.(v_j - v_i) / m_i
+//   with f_ij = 1/2 or the energy-weighted share (energy_share)
 // Every operand that appears for both members of a pair is formed by the same
 // expression on both sides, so F_ji = -F_ij bit for bit.
 // ===========================================================================
-template <class R> struct PassC2 {
+template <class R, bool VAR = false> struct PassC2 {
+  // VAR: the formulation variants (per-side viscosity, energy split) are
+  // compiled in (the default form is compiled without them)
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 128;
   static constexpr int MB0 = 2, MB1 = 3, MB2 = 4;  // resident-block variants
@@ -370,18 +376,20 @@ template <class R> struct PassC2 {
     Common c;
     const R* __restrict__ rec_c2;
     const R* __restrict__ ms;
+    const R* __restrict__ us;  // sorted specific energies (the energy split)
     R* dvdt;
     R* dudt;
     AVParams<R> av;
   };
   struct State {
     R ri[RC::C2];
-    R L, halfL;
+    R L, halfL, u;
     R a[3];
     Acc<R> e;
   };
   __device__ static void begin(const Args& a, int64_t s, State& st) {
     load_rec<RC::C2>(a.rec_c2, s, st.ri);
+    st.u = (VAR && a.av.energy_split) ? a.us[s] : R(0);
     double L = a.c.box_L[a.c.boxid[s]];
     st.L = (R)L;
     st.halfL = (R)(0.5 * L);
@@ -390,19 +398,22 @@ template <class R> struct PassC2 {
   }
   __device__ static const R* src0(const Args& a) { return a.rec_c2; }
   __device__ static const R* src1(const Args&) { return nullptr; }
-  __device__ static void pair_s(const Args& a, State& st, const R* rj, const R*, uint32_t,
+  __device__ static void pair_s(const Args& a, State& st, const R* rj, const R*, uint32_t j,
                                 uint32_t) {
     if (a.c.spec && (st.ri[RC::C2_FLAG] > R(1.5) || rj[RC::C2_FLAG] > R(1.5))) return;  // winds
     R d[3];
     separation(st.ri, rj, st.L, st.halfL, d);
     const R r2 = dot3(d, d);
     R F[3];
-    PairC2<R>::force(st.ri, rj, d, r2, a.av, F);
+    PairC2<R>::template force<VAR>(st.ri, rj, d, r2, a.av, F);
 #pragma unroll
     for (int p = 0; p < 3; ++p) st.a[p] += F[p];
     const R* vi = st.ri + RC::C2_VEL;
     const R* vj = rj + RC::C2_VEL;
-    st.e.add(R(-0.5) * (F[0] * (vi[0] - vj[0]) + F[1] * (vi[1] - vj[1]) + F[2] * (vi[2] - vj[2])));
+    // pair work E_ij = F.(v_j - v_i), formed identically from both sides
+    const R E = -(F[0] * (vi[0] - vj[0]) + F[1] * (vi[1] - vj[1]) + F[2] * (vi[2] - vj[2]));
+    const R f = (VAR && a.av.energy_split) ? energy_share(true, E, st.u, a.us[j]) : R(0.5);
+    st.e.add(f * E);
   }
   __device__ static void end(const Args& a, int64_t s, State& st) {
     const R im = R(1) / a.ms[s];
@@ -426,6 +437,20 @@ int sweep_grid(const Plan* plan, const void* kernel, int block, int smem) {
   int64_t g = (int64_t)plan->num_sms * per_sm;
   if (g > need) g = need;
   return (int)(g > 0 ? g : 1);
+}
+
+// The rate sweep in the default form (all launch variants) or, with a
+// formulation variant switched on, in the form that compiles them in.
+template <class R>
+void launch_rates_sweep(Plan* plan, cudaStream_t st, const typename PassC2<R>::Args& a) {
+  if (plan->p.q_side || plan->p.energy_split) {
+    typename PassC2<R, true>::Args av;
+    static_assert(sizeof(av) == sizeof(a), "same arguments");
+    memcpy(&av, &a, sizeof(a));
+    launch_sweep_plain<PassC2<R, true>>(plan, st, av, "c2_rates");
+  } else {
+    launch_sweep<PassC2<R>>(plan, st, a, "c2_rates");
+  }
 }
 
 template <class R>
@@ -489,9 +514,9 @@ crk_status rates_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R
                               (R)p.relax_dt};
   launch_sweep<PassC1<R>>(plan, st, a1, "c1_density");
   if (do_c2) {
-    typename PassC2<R>::Args a2{c, rec_c2, reinterpret_cast<const R*>(ws + Ly.ms), dvdt, dudt,
-                                make_av<R>(p)};
-    launch_sweep<PassC2<R>>(plan, st, a2, "c2_rates");
+    typename PassC2<R>::Args a2{c, rec_c2, reinterpret_cast<const R*>(ws + Ly.ms), us, dvdt,
+                                dudt, make_av<R>(p)};
+    launch_rates_sweep<R>(plan, st, a2);
   }
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }
@@ -725,9 +750,9 @@ crk_status rates_active_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, 
                               (R)p.Cq,
                               (R)p.relax_dt};
   launch_sweep<PassC1<R>>(plan, st, a1, "c1_density");
-  typename PassC2<R>::Args a2{ca, rec_c2, reinterpret_cast<const R*>(ws + Ly.ms), dvdt, dudt,
+  typename PassC2<R>::Args a2{ca, rec_c2, reinterpret_cast<const R*>(ws + Ly.ms), us, dvdt, dudt,
                               make_av<R>(p)};
-  launch_sweep<PassC2<R>>(plan, st, a2, "c2_rates");
+  launch_rates_sweep<R>(plan, st, a2);
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }
 

@@ -441,9 +441,25 @@ __device__ __forceinline__ void rk_gradient(const R* C, const R* x, R W, R g, bo
 template <class R> struct AVParams {
   R eta_crit, eta_fold, eps2;
   int limiter;
+  int q_side;        // each side's viscosity with its own gradient
+  int energy_split;  // pair work shared by the specific energies
 };
 template <class R> AVParams<R> make_av(const crk_params& p) {
-  return AVParams<R>{(R)p.eta_crit, (R)p.eta_fold, (R)p.eps2, p.limiter};
+  return AVParams<R>{(R)p.eta_crit, (R)p.eta_fold, (R)p.eps2, p.limiter, p.q_side,
+                     p.energy_split};
+}
+
+// Share f_ij of the pair work E_ij that particle i receives (compatible energy,
+// f_ij + f_ji = 1): 1/2, or with the energy split
+// (1 + sgn(E_ij) (u_j - u_i)/(u_i + u_j))/2.  E_ij and the energy difference
+// are formed identically from both sides, so f_ji = 1 - f_ij to rounding.
+template <class R>
+__device__ __forceinline__ R energy_share(bool split, R E, R ui, R uj) {
+  if (!split) return R(0.5);
+  const R su = ui + uj;
+  if (!(su > R(0)) || E == R(0)) return R(0.5);
+  const R q = (uj - ui) / su;
+  return R(0.5) * (R(1) + (E > R(0) ? q : -q));
 }
 
 // The shared pair kernel: returns F (force on i from j, = m_i a_ij) and the
@@ -457,6 +473,7 @@ template <class R> struct PairC2 {
     const R sm = a + b;
     return R(4) * ab / (sm * sm);
   }
+  template <bool VAR = false>
   __device__ static __forceinline__ void force(const R* ri, const R* rj, const R* d, R r2,
                                                const AVParams<R>& av, R* F) {
     const R r = radius(r2);
@@ -501,6 +518,18 @@ template <class R> struct PairC2 {
     muj = muj < R(0) ? muj : R(0);
     const R Qi = mui * (ri[RC::C2_QB] * mui - ri[RC::C2_QA]);
     const R Qj = muj * (rj[RC::C2_QB] * muj - rj[RC::C2_QA]);
+    if (VAR && av.q_side) {
+      // (P_i + P_j)(G_ij - G_ji) + 2 (Q_ij G_ij - Q_ji G_ji), the two products
+      // rounded on their own so that the j side forms exactly the negation
+      const R VV = R(-0.5) * (ri[RC::C2_V] * rj[RC::C2_V]);
+      const R PP = ri[RC::C2_P] + rj[RC::C2_P];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const R qg = rsub(rmul(Qi, Gi[p]), rmul(Qj, Gj[p]));
+        F[p] = VV * radd(rmul(PP, Gi[p] - Gj[p]), R(2) * qg);
+      }
+      return;
+    }
     const R Pi = (ri[RC::C2_P] + rj[RC::C2_P]) + (Qi + Qj);
     const R pre = R(-0.5) * (ri[RC::C2_V] * rj[RC::C2_V]) * Pi;
 #pragma unroll
@@ -518,6 +547,14 @@ void launch_variant(Plan* plan, cudaStream_t st, const typename P::Args& a) {
   typename P::Args b = a;
   b.c.lpt = P::LPT && lpt_worthwhile(plan->ly.nw, (int64_t)grid * P::BLOCK / 32);
   k_sweep<P, MB, MODE><<<grid, P::BLOCK, smem, st>>>(b);
+}
+
+// The plain-load variant with the first resident-block count only (the
+// formulation variants of the rate sweeps, which are not autotuned).
+template <class P>
+void launch_sweep_plain(Plan* plan, cudaStream_t st, const typename P::Args& a, const char* name) {
+  Phase ph(plan, st, name, 1);
+  launch_variant<P, P::MB0, 0>(plan, st, a);
 }
 
 // Variant v of a sweep: v % 3 picks the resident-block count (MB0..MB2),

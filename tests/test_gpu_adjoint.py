@@ -249,3 +249,29 @@ def test_fused_rates_adjoint_matches_separate_calls(precision):
     assert rel(out[1].double().cpu().numpy(), du0) < tol
     for a, b in zip(out[2:], grads):
         assert rel(a.double().cpu().numpy(), b) < tol
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", [dict(energy_split=1), dict(q_side=1),
+                                  dict(energy_split=1, q_side=1)])
+def test_dot_product_formulation_variants(precision, mode):
+    """The adjoint of the variant rates (per-side viscosity, energy split with
+    its dependence on u) against the oracle's JVP in the same mode."""
+    d = synth.unequal_masses(_box(), seed=8)
+    n = d["h"].shape[0]
+    ga, gu = synth.cotangents(n, seed=4)
+    grads, _, _ = _gpu_adjoint(d, precision, ga, gu, **mode)
+    rng = np.random.default_rng(13)
+    dirs = _directions(d, rng, "all")
+    _, tan = oracle.jvp(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], tx=dirs[0], tv=dirs[1],
+                        tu=dirs[2], th=dirs[3], params=oracle.default_params(**mode),
+                        want=("dvdt", "dudt"))
+    lhs = (ga * tan["dvdt"]).sum() + (gu * tan["dudt"]).sum()
+    rhs, scale = _pairing(grads, dirs)
+    assert abs(lhs - rhs) <= TOL[precision] * scale, (mode, lhs, rhs, scale)
+    # the u direction alone exercises the split's dependence on u
+    dirs = _directions(d, rng, "u")
+    _, tan = oracle.jvp(d["x"], d["h"], d["m"], d["v"], d["u"], d["L"], tu=dirs[2],
+                        params=oracle.default_params(**mode), want=("dvdt", "dudt"))
+    lhs = (ga * tan["dvdt"]).sum() + (gu * tan["dudt"]).sum()
+    rhs, scale = _pairing(grads, dirs)
+    assert abs(lhs - rhs) <= TOL[precision] * scale, (mode, lhs, rhs, scale)

@@ -370,3 +370,26 @@ def test_graph_replay_equals_eager(precision):
     assert s.poll() == 0
     for a, b in zip(eager, outs + grads):
         assert torch.equal(a, b)
+
+
+# ------------------------------------------------------------------ formulation variants
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", [dict(energy_split=1), dict(q_side=1),
+                                  dict(energy_split=1, q_side=1)])
+def test_formulation_variants_parity_and_conservation(precision, mode):
+    """Energy split weighted by the specific energies and per-side viscosity
+    (Sec. 2.1, the cited formulation's variants): rates against the oracle in
+    the same mode, and momentum and energy conserved, with unequal masses."""
+    d = synth.load("lognormal32m")
+    gpu, _ = run_forward(d, precision, **mode)
+    assert gpu["status"] == 0
+    ora = _oracle_all(d, **mode)
+    err = compare(gpu, ora, keys=("dvdt", "dudt"), coef=False)
+    for k, e in err.items():
+        assert e < TOL[precision], (mode, k, err)
+    m, v, a, du = d["m"], d["v"], gpu["dvdt"], gpu["dudt"]
+    p = np.abs((m * a).sum(1)).max() / np.abs(m * a).sum()
+    e = abs((m * (v * a).sum(0)).sum() + (m * du).sum()) / (
+        np.abs(m * (v * a).sum(0)).sum() + np.abs(m * du).sum())
+    assert p < (1e-13 if precision == "fp64" else 1e-6), p
+    assert e < (1e-13 if precision == "fp64" else 1e-6), e
