@@ -372,7 +372,7 @@ crk_status crk_cool_exact(crk_plan* plan, crk_stream_t stream, int64_t n,
  * ring with cp.async (variants 3-5), loaded one list entry ahead into a
  * register double buffer (variants 6-8), or gathered four records at a time by
  * the tensor memory accelerator (TMA tile::gather4 copies) into a per-warp
- * four-stage shared-memory ring that completes on mbarriers (variants 9-11).
+ * two-stage shared-memory ring that completes on mbarriers (variants 9-11).
  * This call runs crk_moments, crk_rates and, when g_dvdt and g_dudt are given,
  * crk_adjoint on the caller's data with each variant `repeats` times, times
  * every sweep with CUDA events and keeps the fastest variant per sweep in the

@@ -146,14 +146,13 @@ constexpr int sweep_regs(int block, int minb) {
 constexpr int sweep_regs_tma(int block, int minb) { return sweep_regs(block, minb); }
 
 // ---------------------------------------------------------------------------
-// Neighbor records by TMA gather (load mode 3).  Each warp owns a ring of
-// Gather<P>::NST stages in shared memory.  For list step k the 32 lanes' neighbor indices are
+// Neighbor records by TMA gather (load mode 3).  Each warp owns a two-stage
+// ring in shared memory.  For list step k the 32 lanes' neighbor indices are
 // grouped by four and every fourth lane issues one tile::gather4 bulk tensor
 // copy per record array: four rows of the record array (one row per
 // particle, the tensor map's box one row high) land in shared memory, and
 // the copies of a stage complete one mbarrier with their byte count.  The
-// records of steps k+1 .. k+NST-1 are in flight while the pairs of step k are
-// evaluated.
+// records of step k+1 are in flight while the pairs of step k are evaluated.
 // The copies go from L2 into shared memory without passing the L1 tag stage
 // or the load/store pipe, where the per-lane gathers of the other modes spend
 // most of their time.  Every wait on an mbarrier is bounded: a wait that gives
@@ -162,7 +161,6 @@ constexpr int sweep_regs_tma(int block, int minb) { return sweep_regs(block, min
 // ---------------------------------------------------------------------------
 template <class P> struct Gather {
   using R = typename P::Real;
-  static constexpr int NST = 4;                                   // ring stages per warp
   static constexpr int RB0 = P::SW0 * (int)sizeof(R);             // row bytes, source 0
   static constexpr int RB1 = P::SW1 * (int)sizeof(R);             // row bytes, source 1
   static constexpr int G0 = round_up(4 * RB0, 128);                // one gather4, 128-B aligned
@@ -170,7 +168,7 @@ template <class P> struct Gather {
   static constexpr int STAGE = 8 * (G0 + G1);                      // 32 lanes per warp step
   static constexpr int TX = 32 * (RB0 + RB1);                      // bytes that land per stage
   static constexpr int WARPS = P::BLOCK / 32;
-  static constexpr size_t bytes = (size_t)WARPS * (NST * STAGE + 8 * NST) + 128;
+  static constexpr size_t bytes = (size_t)WARPS * (2 * STAGE + 16) + 128;
   static_assert(RB0 % 16 == 0 && RB1 % 16 == 0, "rows are whole 16-byte vectors");
 };
 
@@ -193,6 +191,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   for (int it = 0; it < (1 << 20) && !ok; ++it) ok = mbar_try(bar, parity);
   return __all_sync(kFull, ok);
 }
+template <class R> struct TmaType;
+template <> struct TmaType<float> { static constexpr int code = 0; };
+template <> struct TmaType<double> { static constexpr int code = 1; };
 
 template <class P, int MINB>
 __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs_tma(P::BLOCK, MINB))
@@ -200,19 +201,17 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs_tma(P::BLOCK,
                 const __grid_constant__ CUtensorMap tm1) {
   using Real = typename P::Real;
   using G = Gather<P>;
-  constexpr int NST = G::NST;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int32_t* q = &a.c.hdr->queue[P::QUEUE];
   extern __shared__ unsigned char tma_smem[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(tma_smem) + 127) & ~uintptr_t(127));
-  unsigned char* ring = base + (size_t)wib * NST * G::STAGE;
-  const uint32_t bar_base =
-      smem_u32(base + (size_t)G::WARPS * NST * G::STAGE + (size_t)wib * 8 * NST);
+  unsigned char* ring = base + (size_t)wib * 2 * G::STAGE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + (size_t)G::WARPS * 2 * G::STAGE) + 2 * wib;
+  const uint32_t bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
   if (lane == 0) {
-#pragma unroll
-    for (int st = 0; st < NST; ++st)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_base + 8 * st) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -224,13 +223,14 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs_tma(P::BLOCK,
     const int g = lane & ~3;
     const uint32_t r0 = __shfl_sync(kFull, row, g), r1 = __shfl_sync(kFull, row, g + 1),
                    r2 = __shfl_sync(kFull, row, g + 2), r3 = __shfl_sync(kFull, row, g + 3);
-    const uint32_t bar = bar_base + 8 * st;
+    const uint32_t bar = st ? bar1 : bar0;
     if (lane == 0)
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                    "r"((uint32_t)G::TX)
                    : "memory");
-    __syncwarp();  // (the stage's earlier generic reads are done: see the loop's end)
+    __syncwarp();
     if ((lane & 3) == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       unsigned char* stage = ring + (size_t)st * G::STAGE;
       const uint32_t d0 = smem_u32(stage + (lane >> 2) * G::G0);
       asm volatile(
@@ -278,34 +278,34 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs_tma(P::BLOCK,
     const uint32_t* col = a.c.ell + (s >> 5) * a.c.cap_pp * 32 + (s & 31);
     const int tot = lg + ls;
     const int wmax = __reduce_max_sync(kFull, tot);
-    // the list entry of step k (the particle itself past its list or for a
-    // bad entry of the bounds-checked build)
+    // the record index of list step k (the particle itself past its list or
+    // for a bad entry of the bounds-checked build), and the full entry
     auto entry = [&](int k) -> uint32_t {
       if (k >= tot) return (uint32_t)s;
       const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
       const uint32_t e = __ldg(col + slot * 32);
       return index_ok(a.c.hdr, e & kIdxMask, a.c.n) ? e : (uint32_t)s;
     };
-    // prologue: the first NST - 1 steps in flight
-#pragma unroll
-    for (int k = 0; k < NST - 1; ++k)
-      if (k < wmax) issue(k, entry(k) & kIdxMask);
+    uint32_t e_next = wmax > 0 ? entry(0) : 0u;
+    if (wmax > 0) issue(0, e_next & kIdxMask);
     bool failed = false;
     for (int k = 0; k < wmax; ++k) {
-      const int cur = k % NST;
-      if (k + NST - 1 < wmax) issue((k + NST - 1) % NST, entry(k + NST - 1) & kIdxMask);
-      if (!mbar_wait(bar_base + 8 * cur, (parity >> cur) & 1u)) {
+      const uint32_t e = e_next;
+      const int cur = k & 1;
+      if (k + 1 < wmax) {
+        e_next = entry(k + 1);
+        issue(cur ^ 1, e_next & kIdxMask);
+      }
+      if (!mbar_wait(cur ? bar1 : bar0, (parity >> cur) & 1u)) {
         failed = true;
-        // the later steps' copies are in flight: let them land (bounded)
-        for (int k2 = k + 1; k2 < wmax && k2 < k + NST; ++k2) {
-          const int st2 = k2 % NST;
-          (void)mbar_wait(bar_base + 8 * st2, (parity >> st2) & 1u);
+        if (k + 1 < wmax) {  // the other stage's copies are in flight: let them land
+          const int oth = cur ^ 1;
+          (void)mbar_wait(oth ? bar1 : bar0, (parity >> oth) & 1u);
         }
         break;
       }
       parity ^= 1u << cur;
       if (k < tot) {
-        const uint32_t e = entry(k);
         const unsigned char* stage = ring + (size_t)cur * G::STAGE;
         Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
         const float4* p0 = reinterpret_cast<const float4*>(stage + (lane >> 2) * G::G0 +
@@ -330,6 +330,8 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs_tma(P::BLOCK,
     if (live) P::end(a, s, st);
   }
 }
+
+
 
 // Persistent sweep: warps pull 32-particle work items from an atomic queue --
 // 32 consecutive sorted particles, or 32 entries of a work list (the active
