@@ -369,10 +369,8 @@ crk_status crk_cool_exact(crk_plan* plan, crk_stream_t stream, int64_t n,
  * blocks per SM (so three register caps and occupancies; variant % 3), each
  * with the neighbor records read straight from global memory when the pair is
  * evaluated (variants 0-2), copied ahead through a per-thread shared-memory
- * ring with cp.async (variants 3-5), loaded one list entry ahead into a
- * register double buffer (variants 6-8), or gathered four records at a time by
- * the tensor memory accelerator (TMA tile::gather4 copies) into a per-warp
- * two-stage shared-memory ring that completes on mbarriers (variants 9-11).
+ * ring with cp.async (variants 3-5), or loaded one list entry ahead into a
+ * register double buffer (variants 6-8).
  * This call runs crk_moments, crk_rates and, when g_dvdt and g_dudt are given,
  * crk_adjoint on the caller's data with each variant `repeats` times, times
  * every sweep with CUDA events and keeps the fastest variant per sweep in the
@@ -381,7 +379,7 @@ crk_status crk_cool_exact(crk_plan* plan, crk_stream_t stream, int64_t n,
  * choice_out (optional, host int32[8]) receives the chosen variant per sweep,
  * ms_out (optional, host float[8][CRK_TUNE_VARIANTS]) the mean milliseconds of
  * every variant.  Synchronises.  Requires a built workspace. */
-#define CRK_TUNE_VARIANTS 12
+#define CRK_TUNE_VARIANTS 9
 crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
                         const void* v, const void* u, const void* g_dvdt, const void* g_dudt,
                         int32_t repeats, int32_t* choice_out, float* ms_out);
@@ -410,8 +408,7 @@ typedef struct {
   int64_t tree_tests;     /* tree nodes tested by the last list build (counting pass) */
   int64_t bucket_tests;   /* candidate buckets (8 particles each) tested by that pass */
   int32_t status;         /* device status word (not cleared) */
-  int32_t tma_fallbacks;  /* TMA-gather launches (variants 9-11) that ran with plain loads
-                             because the driver rejected a tensor map; 0 on a working device */
+  int32_t reserved;
 } crk_stats;
 
 /* Statistics of the last build.  Synchronises `stream`. */

@@ -35,7 +35,7 @@ class crk_stats(C.Structure):
                 ("union_pairs", C.c_int64), ("list_slots", C.c_int64),
                 ("list_capacity", C.c_int64), ("tree_nodes", C.c_int64),
                 ("launches", C.c_int64), ("tree_tests", C.c_int64), ("bucket_tests", C.c_int64),
-                ("status", C.c_int32), ("tma_fallbacks", C.c_int32)]
+                ("status", C.c_int32), ("reserved", C.c_int32)]
 
 
 class crk_kernel_time(C.Structure):
@@ -100,7 +100,7 @@ _SIGS = {
                             _VP, _VP, _VP, _VP, C.c_double, _VP, _VP, _VP]),
 }
 CRK_STATIC_MAX_PARTICLES = 65536
-CRK_TUNE_VARIANTS = 12  # launch variants per sweep (include/crk.h)
+CRK_TUNE_VARIANTS = 9  # launch variants per sweep (include/crk.h)
 
 _lib = None
 

@@ -287,8 +287,8 @@ template <class R, bool VAR = false> struct PassA2 {
     st.fa[0] = st.fa[1] = st.fa[2] = R(0);
     st.fe = Acc<R>();
   }
-  __host__ __device__ static const R* src0(const Args& a) { return a.rec_c2; }
-  __host__ __device__ static const R* src1(const Args& a) { return a.rec_ab; }
+  __device__ static const R* src0(const Args& a) { return a.rec_c2; }
+  __device__ static const R* src1(const Args& a) { return a.rec_ab; }
   __device__ static void pair_s(const Args& a, State& st, const R* rj, const R* abj, uint32_t j,
                                 uint32_t) {
     const R* ri = st.ri;
@@ -638,8 +638,8 @@ template <class R> struct PassA1 {
     rk_gradient_rev(C, dd, W, g, true, Gb, Cb ? Cb : Cdummy, ddb, Wb, gb);
     hb += wendland_rev(Wb, gb, W, g, gg, r2, ih, dd, ddb);
   }
-  __host__ __device__ static const R* src0(const Args& a) { return a.rec_a1; }
-  __host__ __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static const R* src0(const Args& a) { return a.rec_a1; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
   __device__ static void pair_s(const Args& a, State& st, const R* rj, const R*, uint32_t j,
                                 uint32_t e) {
     R d[3];
@@ -808,8 +808,8 @@ template <class R> struct PassAB2 {
     for (int k = 0; k < 3; ++k) ddb[k] += db[k];
     return hpart;
   }
-  __host__ __device__ static const R* src0(const Args& a) { return a.rec_a2; }
-  __host__ __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static const R* src0(const Args& a) { return a.rec_a2; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
   __device__ static void pair_s(const Args& a, State& st, const R* rj, const R*, uint32_t j,
                                 uint32_t e) {
     R d[3];
@@ -895,8 +895,8 @@ template <class R> struct PassAB1 {
     st.L = (R)L;
     st.halfL = (R)(0.5 * L);
   }
-  __host__ __device__ static const R* src0(const Args& a) { return a.rec_a3; }
-  __host__ __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static const R* src0(const Args& a) { return a.rec_a3; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
   __device__ static void pair_s(const Args& a, State& st, const R* rj, const R*, uint32_t j,
                                 uint32_t e) {
     R d[3];

@@ -4,7 +4,6 @@
 #include <cstring>
 #include <new>
 
-#include <cudaTypedefs.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "crk_internal.cuh"
@@ -103,40 +102,6 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.seq_order = take(4 * NW + 4);
   L.total = o;
   return L;
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (the
-// library links the runtime statically and the driver only at run time)
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      f = nullptr;
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  }();
-  return fn;
-}
-
-bool encode_record_rows(CUtensorMap* tm, const void* base, int64_t rows, int row_words,
-                        int elem_bytes) {
-  const auto enc = tensor_map_encoder();
-  if (!enc || !base || rows < 1 || rows > (int64_t(1) << 31) || row_words < 1 ||
-      row_words > 256 || (reinterpret_cast<uintptr_t>(base) & 15) ||
-      ((int64_t)row_words * elem_bytes) % 16 != 0)
-    return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)row_words, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)row_words * (cuuint64_t)elem_bytes};
-  const cuuint32_t box[2] = {(cuuint32_t)row_words, 1u};
-  const cuuint32_t estr[2] = {1u, 1u};
-  const CUtensorMapDataType dt =
-      elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  return enc(tm, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 static bool params_ok(const crk_params& p) {
@@ -656,7 +621,6 @@ crk_status crk_stats_get(crk_plan* plan, crk_stream_t stream, void* ws, crk_stat
   out->tree_tests = (int64_t)h.nbr_nodes;
   out->bucket_tests = (int64_t)h.nbr_buckets;
   out->status = h.status;
-  out->tma_fallbacks = P.tma_fallbacks;
   return CRK_OK;
 }
 

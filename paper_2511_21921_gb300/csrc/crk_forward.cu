@@ -72,8 +72,8 @@ template <class R> struct PassB1 {
     st.halfL = (R)(0.5 * L);
     st.sum = R(0);
   }
-  __host__ __device__ static const R* src0(const Args& a) { return a.rec_b1; }
-  __host__ __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static const R* src0(const Args& a) { return a.rec_b1; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
   __device__ static void pair_s(const Args& a, State& st, const R* r, const R*, uint32_t j,
                                 uint32_t) {
     R d[3];
@@ -154,8 +154,8 @@ template <class R> struct PassB2 {
 #pragma unroll
     for (int k = 0; k < 10; ++k) st.S3[k] = R(0);
   }
-  __host__ __device__ static const R* src0(const Args& a) { return a.rec_b2; }
-  __host__ __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static const R* src0(const Args& a) { return a.rec_b2; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
   __device__ static void pair_s(const Args& a, State& st, const R* r, const R*, uint32_t j,
                                 uint32_t) {
     if (r[RC::B2_SP] != R(0)) return;  // the corrections reproduce over the gas
@@ -285,8 +285,8 @@ template <class R> struct PassC1 {
 #pragma unroll
     for (int k = 0; k < 9; ++k) st.gv[k] = R(0);
   }
-  __host__ __device__ static const R* src0(const Args& a) { return a.rec_c1; }
-  __host__ __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static const R* src0(const Args& a) { return a.rec_c1; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
   __device__ static void pair_s(const Args& a, State& st, const R* r, const R*, uint32_t j,
                                 uint32_t) {
     R d[3];
@@ -396,8 +396,8 @@ template <class R, bool VAR = false> struct PassC2 {
     st.a[0] = st.a[1] = st.a[2] = R(0);
     st.e = Acc<R>();
   }
-  __host__ __device__ static const R* src0(const Args& a) { return a.rec_c2; }
-  __host__ __device__ static const R* src1(const Args&) { return nullptr; }
+  __device__ static const R* src0(const Args& a) { return a.rec_c2; }
+  __device__ static const R* src1(const Args&) { return nullptr; }
   __device__ static void pair_s(const Args& a, State& st, const R* rj, const R*, uint32_t j,
                                 uint32_t) {
     if (a.c.spec && (st.ri[RC::C2_FLAG] > R(1.5) || rj[RC::C2_FLAG] > R(1.5))) return;  // winds

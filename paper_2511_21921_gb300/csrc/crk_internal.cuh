@@ -5,8 +5,6 @@
 #include <algorithm>
 #include <utility>
 
-#include <cuda.h>
-
 #include "crk_common.cuh"
 
 struct crk_plan;
@@ -37,9 +35,6 @@ struct Plan {
   int32_t nb = 0;
   Tuning tune[16];
   int variant[16] = {};  // launch variant per sweep: v % 3 -> MB0..MB2, v / 3 -> load mode
-  // TMA gather launches that fell back to plain loads because the driver
-  // rejected a tensor map (never expected; reported by crk_stats_get)
-  int tma_fallbacks = 0;
   // instrumentation
   long long launches = 0;
   bool timing = false;
@@ -110,12 +105,6 @@ crk_status adjoint_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const
 
 // persistent grid size for a sweep kernel
 int sweep_grid(const Plan* plan, const void* kernel, int block, int smem);
-
-// Tensor map of an array of `rows` records of `row_words` elements (float:
-// elem_bytes 4, double: 8), one record per row, for TMA gathers of whole
-// records (box: one row).  False when the driver rejects it.
-bool encode_record_rows(CUtensorMap* tm, const void* base, int64_t rows, int row_words,
-                        int elem_bytes);
 
 }  // namespace crk
 

@@ -143,195 +143,6 @@ constexpr int sweep_regs(int block, int minb) {
   const int r = (65536 / (minb * block)) & ~7;
   return r > 255 ? 255 : r;
 }
-constexpr int sweep_regs_tma(int block, int minb) { return sweep_regs(block, minb); }
-
-// ---------------------------------------------------------------------------
-// Neighbor records by TMA gather (load mode 3).  Each warp owns a two-stage
-// ring in shared memory.  For list step k the 32 lanes' neighbor indices are
-// grouped by four and every fourth lane issues one tile::gather4 bulk tensor
-// copy per record array: four rows of the record array (one row per
-// particle, the tensor map's box one row high) land in shared memory, and
-// the copies of a stage complete one mbarrier with their byte count.  The
-// records of step k+1 are in flight while the pairs of step k are evaluated.
-// The copies go from L2 into shared memory without passing the L1 tag stage
-// or the load/store pipe, where the per-lane gathers of the other modes spend
-// most of their time.  Every wait on an mbarrier is bounded: a wait that gives
-// up sets CRK_ETIMEOUT, waits (bounded again) for the warp's copies still in
-// flight and ends the warp's work.
-// ---------------------------------------------------------------------------
-template <class P> struct Gather {
-  using R = typename P::Real;
-  static constexpr int RB0 = P::SW0 * (int)sizeof(R);             // row bytes, source 0
-  static constexpr int RB1 = P::SW1 * (int)sizeof(R);             // row bytes, source 1
-  static constexpr int G0 = round_up(4 * RB0, 128);                // one gather4, 128-B aligned
-  static constexpr int G1 = RB1 > 0 ? round_up(4 * RB1, 128) : 0;
-  static constexpr int STAGE = 8 * (G0 + G1);                      // 32 lanes per warp step
-  static constexpr int TX = 32 * (RB0 + RB1);                      // bytes that land per stage
-  static constexpr int WARPS = P::BLOCK / 32;
-  static constexpr size_t bytes = (size_t)WARPS * (2 * STAGE + 16) + 128;
-  static_assert(RB0 % 16 == 0 && RB1 % 16 == 0, "rows are whole 16-byte vectors");
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait for phase `parity` of the mbarrier at `bar` (whole warp agrees)
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  bool ok = false;
-  for (int it = 0; it < (1 << 20) && !ok; ++it) ok = mbar_try(bar, parity);
-  return __all_sync(kFull, ok);
-}
-template <class R> struct TmaType;
-template <> struct TmaType<float> { static constexpr int code = 0; };
-template <> struct TmaType<double> { static constexpr int code = 1; };
-
-template <class P, int MINB>
-__global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs_tma(P::BLOCK, MINB))
-    k_sweep_tma(const __grid_constant__ typename P::Args a, const __grid_constant__ CUtensorMap tm0,
-                const __grid_constant__ CUtensorMap tm1) {
-  using Real = typename P::Real;
-  using G = Gather<P>;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  int32_t* q = &a.c.hdr->queue[P::QUEUE];
-  extern __shared__ unsigned char tma_smem[];
-  unsigned char* base = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(tma_smem) + 127) & ~uintptr_t(127));
-  unsigned char* ring = base + (size_t)wib * 2 * G::STAGE;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + (size_t)G::WARPS * 2 * G::STAGE) + 2 * wib;
-  const uint32_t bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
-  if (lane == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  __syncwarp();
-  uint32_t parity = 0u;  // bit st: the phase parity stage st waits for next
-  // issue the copies of one list step into stage st; `row` is this lane's
-  // record index for that step
-  auto issue = [&](int st, uint32_t row) {
-    const int g = lane & ~3;
-    const uint32_t r0 = __shfl_sync(kFull, row, g), r1 = __shfl_sync(kFull, row, g + 1),
-                   r2 = __shfl_sync(kFull, row, g + 2), r3 = __shfl_sync(kFull, row, g + 3);
-    const uint32_t bar = st ? bar1 : bar0;
-    if (lane == 0)
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                   "r"((uint32_t)G::TX)
-                   : "memory");
-    __syncwarp();
-    if ((lane & 3) == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      unsigned char* stage = ring + (size_t)st * G::STAGE;
-      const uint32_t d0 = smem_u32(stage + (lane >> 2) * G::G0);
-      asm volatile(
-          "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes"
-          " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(d0),
-          "l"(reinterpret_cast<uint64_t>(&tm0)), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3),
-          "r"(bar)
-          : "memory");
-      if constexpr (G::RB1 > 0) {
-        const uint32_t d1 = smem_u32(stage + 8 * G::G0 + (lane >> 2) * G::G1);
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(d1),
-            "l"(reinterpret_cast<uint64_t>(&tm1)), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3),
-            "r"(bar)
-            : "memory");
-      }
-    }
-  };
-  const int32_t* its = a.c.items ? a.c.items : (P::BALANCE ? a.c.bal : nullptr);
-  const int64_t nlist = its ? (int64_t)*(a.c.items ? a.c.n_items : a.c.n_bal) : 0;
-  const int64_t nwork = its ? (nlist + 31) / 32 : a.c.nw;
-  for (;;) {
-    int w = 0;
-    if (lane == 0) w = atomicAdd(q, 1);
-    w = __shfl_sync(kFull, w, 0);
-    if (w >= nwork) break;
-    const int64_t wi = (P::LPT && !P::BALANCE && a.c.lpt && !a.c.items) ? a.c.seq_order[w] : w;
-    int64_t s = wi * 32 + lane;
-    bool live = s < a.c.n;
-    if (its) {
-      if (P::LPT && a.c.lpt && !a.c.items) s = (int64_t)a.c.bal_order[w] * 32 + lane;
-      live = s < nlist;
-      s = live ? its[s] : 0;
-      if (live && !index_ok(a.c.hdr, s, a.c.n)) live = false, s = 0;
-    }
-    if (!live) s = 0;  // a valid row for the padding copies
-    typename P::State st;
-    int lg = 0, ls = 0;
-    if (live) {
-      P::begin(a, s, st);
-      lg = a.c.cnt_g[s];
-      ls = P::GATHER ? 0 : a.c.cnt_s[s];
-    }
-    const uint32_t* col = a.c.ell + (s >> 5) * a.c.cap_pp * 32 + (s & 31);
-    const int tot = lg + ls;
-    const int wmax = __reduce_max_sync(kFull, tot);
-    // the record index of list step k (the particle itself past its list or
-    // for a bad entry of the bounds-checked build), and the full entry
-    auto entry = [&](int k) -> uint32_t {
-      if (k >= tot) return (uint32_t)s;
-      const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
-      const uint32_t e = __ldg(col + slot * 32);
-      return index_ok(a.c.hdr, e & kIdxMask, a.c.n) ? e : (uint32_t)s;
-    };
-    uint32_t e_next = wmax > 0 ? entry(0) : 0u;
-    if (wmax > 0) issue(0, e_next & kIdxMask);
-    bool failed = false;
-    for (int k = 0; k < wmax; ++k) {
-      const uint32_t e = e_next;
-      const int cur = k & 1;
-      if (k + 1 < wmax) {
-        e_next = entry(k + 1);
-        issue(cur ^ 1, e_next & kIdxMask);
-      }
-      if (!mbar_wait(cur ? bar1 : bar0, (parity >> cur) & 1u)) {
-        failed = true;
-        if (k + 1 < wmax) {  // the other stage's copies are in flight: let them land
-          const int oth = cur ^ 1;
-          (void)mbar_wait(oth ? bar1 : bar0, (parity >> oth) & 1u);
-        }
-        break;
-      }
-      parity ^= 1u << cur;
-      if (k < tot) {
-        const unsigned char* stage = ring + (size_t)cur * G::STAGE;
-        Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
-        const float4* p0 = reinterpret_cast<const float4*>(stage + (lane >> 2) * G::G0 +
-                                                           (lane & 3) * G::RB0);
-#pragma unroll
-        for (int v = 0; v < G::RB0 / 16; ++v) reinterpret_cast<float4*>(r0)[v] = p0[v];
-        if constexpr (G::RB1 > 0) {
-          const float4* p1 = reinterpret_cast<const float4*>(stage + 8 * G::G0 +
-                                                             (lane >> 2) * G::G1 +
-                                                             (lane & 3) * G::RB1);
-#pragma unroll
-          for (int v = 0; v < G::RB1 / 16; ++v) reinterpret_cast<float4*>(r1)[v] = p1[v];
-        }
-        P::pair_s(a, st, r0, r1, e & kIdxMask, e);
-      }
-      __syncwarp();  // every lane is done with this stage before it is refilled
-    }
-    if (failed) {
-      if (lane == 0) set_status(a.c.hdr, CRK_ETIMEOUT);
-      return;
-    }
-    if (live) P::end(a, s, st);
-  }
-}
-
-
 
 // Persistent sweep: warps pull 32-particle work items from an atomic queue --
 // 32 consecutive sorted particles, or 32 entries of a work list (the active
@@ -738,31 +549,6 @@ void launch_variant(Plan* plan, cudaStream_t st, const typename P::Args& a) {
   k_sweep<P, MB, MODE><<<grid, P::BLOCK, smem, st>>>(b);
 }
 
-// Load mode 3: the TMA gather kernel with tensor maps of the pass's record
-// arrays (one row per sorted particle).
-template <class P, int MB>
-void launch_variant_tma(Plan* plan, cudaStream_t st, const typename P::Args& a) {
-  using R = typename P::Real;
-  CUtensorMap t0, t1;
-  const int64_t n = plan->ly.n;
-  bool ok = encode_record_rows(&t0, P::src0(a), n, P::SW0, (int)sizeof(R));
-  if (P::SW1 > 0) ok = ok && encode_record_rows(&t1, P::src1(a), n, P::SW1, (int)sizeof(R));
-  else t1 = t0;
-  if (!ok) {
-    ++plan->tma_fallbacks;
-    launch_variant<P, MB, 0>(plan, st, a);
-    return;
-  }
-  const size_t smem = Gather<P>::bytes;
-  const void* fn = (const void*)k_sweep_tma<P, MB>;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int grid = sweep_grid(plan, fn, P::BLOCK, (int)smem);
-  typename P::Args b = a;
-  b.c.lpt = P::LPT && lpt_worthwhile(plan->ly.nw, (int64_t)grid * P::BLOCK / 32);
-  k_sweep_tma<P, MB><<<grid, P::BLOCK, smem, st>>>(b, t0, t1);
-}
-
 // The plain-load variant with the first resident-block count only (the
 // formulation variants of the rate sweeps, which are not autotuned).
 template <class P>
@@ -773,7 +559,7 @@ void launch_sweep_plain(Plan* plan, cudaStream_t st, const typename P::Args& a, 
 
 // Variant v of a sweep: v % 3 picks the resident-block count (MB0..MB2),
 // v / 3 the mode (0 plain loads, 1 shared-memory ring, 2 register double
-// buffer, 3 TMA gathers into a shared-memory ring).
+// buffer).
 template <class P>
 void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const char* name) {
   const int v = plan->variant[P::QUEUE];
@@ -787,9 +573,6 @@ void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const 
     case 6: launch_variant<P, P::MB0, 2>(plan, st, a); break;
     case 7: launch_variant<P, P::MB1, 2>(plan, st, a); break;
     case 8: launch_variant<P, P::MB2, 2>(plan, st, a); break;
-    case 9: launch_variant_tma<P, P::MB0>(plan, st, a); break;
-    case 10: launch_variant_tma<P, P::MB1>(plan, st, a); break;
-    case 11: launch_variant_tma<P, P::MB2>(plan, st, a); break;
     default: launch_variant<P, P::MB0, 0>(plan, st, a); break;
   }
 }

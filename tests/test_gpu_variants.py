@@ -1,7 +1,6 @@
 """Every compiled launch variant of the eight neighbor sweeps -- three register
-caps times four ways of bringing the neighbor records to the pair arithmetic
-(plain loads, shared-memory ring, register double buffer, TMA gathers into a
-shared-memory ring) -- gives the oracle's
+caps times three ways of bringing the neighbor records to the pair arithmetic
+(plain loads, shared-memory ring, register double buffer) -- gives the oracle's
 results: the forward fields and rates element by element, the adjoint through
 a dot test against the oracle's forward-mode derivative, and the active-set
 path, whose sweeps walk a compacted work list instead of consecutive warps."""
@@ -59,8 +58,6 @@ def test_every_variant_matches_oracle(precision):
         rhs = sum(x.sum() for x in terms)
         scale = sum(np.abs(x).sum() for x in terms)
         assert abs(lhs - rhs) <= ADJ_TOL[precision] * scale, (v, lhs, rhs)
-    # the TMA-gather variants ran as such (no tensor map was rejected)
-    assert s.stats()["tma_fallbacks"] == 0
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
