@@ -365,17 +365,12 @@ crk_status crk_cool_exact(crk_plan* plan, crk_stream_t stream, int64_t n,
 
 /* Autotuner for the launch shapes of the eight neighbor sweeps (volume,
  * moments, density, rates and the four adjoint sweeps).  Each sweep is
- * compiled in nine launch variants: three minimum numbers of resident blocks
- * per SM (so three register caps and occupancies; variant % 3), each with the
- * neighbor records read straight from global memory when the pair is
+ * compiled in CRK_TUNE_VARIANTS variants: three minimum numbers of resident
+ * blocks per SM (so three register caps and occupancies; variant % 3), each
+ * with the neighbor records read straight from global memory when the pair is
  * evaluated (variants 0-2), copied ahead through a per-thread shared-memory
  * ring with cp.async (variants 3-5), or loaded one list entry ahead into a
- * register double buffer (variants 6-8).  Variants 9-17 are variants 0-8 of
- * the union sweeps (rates and the adjoint sweeps) walking the warp-aligned
- * union lists: the build reorders the lists of every 32 consecutive particles
- * so that lanes sharing a neighbor take it in the same step (the same terms in
- * each sum, in another order); for the volume, moment and density sweeps they
- * equal variants 0-8.
+ * register double buffer (variants 6-8).
  * This call runs crk_moments, crk_rates and, when g_dvdt and g_dudt are given,
  * crk_adjoint on the caller's data with each variant `repeats` times, times
  * every sweep with CUDA events and keeps the fastest variant per sweep in the
@@ -384,7 +379,7 @@ crk_status crk_cool_exact(crk_plan* plan, crk_stream_t stream, int64_t n,
  * choice_out (optional, host int32[8]) receives the chosen variant per sweep,
  * ms_out (optional, host float[8][CRK_TUNE_VARIANTS]) the mean milliseconds of
  * every variant.  Synchronises.  Requires a built workspace. */
-#define CRK_TUNE_VARIANTS 18
+#define CRK_TUNE_VARIANTS 9
 crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
                         const void* v, const void* u, const void* g_dvdt, const void* g_dudt,
                         int32_t repeats, int32_t* choice_out, float* ms_out);

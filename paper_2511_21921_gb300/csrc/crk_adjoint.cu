@@ -231,7 +231,6 @@ template <class R, bool VAR = false> struct PassA2 {
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 5, MB2 = 6;  // resident-block variants
   static constexpr int QUEUE = Q_A_C2;
-  static constexpr bool ALIGNABLE = true;  // union sweep that can walk the aligned lists
   using Real = R;
   static constexpr int SW0 = Rec<R>::C2, SW1 = 4;  // words staged per neighbor
   static constexpr bool LPT = true;   // items longest first
@@ -558,7 +557,6 @@ template <class R> struct PassA1 {
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 6, MB2 = 8;  // resident-block variants
   static constexpr int QUEUE = Q_A_C1;
-  static constexpr bool ALIGNABLE = true;  // union sweep that can walk the aligned lists
   using Real = R;
   static constexpr int SW0 = ARec<R>::A1, SW1 = 0;  // words staged per neighbor
   static constexpr bool LPT = false;  // queue order (longest first measured slower here)
@@ -722,7 +720,6 @@ template <class R> struct PassAB2 {
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 10, MB2 = 12;  // resident-block variants
   static constexpr int QUEUE = Q_A_B2;
-  static constexpr bool ALIGNABLE = true;  // union sweep that can walk the aligned lists
   using Real = R;
   static constexpr int SW0 = ARec<R>::A2, SW1 = 0;  // words staged per neighbor
   static constexpr bool LPT = false;  // queue order (longest first measured slower here)
@@ -870,7 +867,6 @@ template <class R> struct PassAB1 {
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 14, MB2 = 16;  // resident-block variants
   static constexpr int QUEUE = Q_A_B1;
-  static constexpr bool ALIGNABLE = true;  // union sweep that can walk the aligned lists
   using Real = R;
   static constexpr int SW0 = ARec<R>::A3, SW1 = 0;  // words staged per neighbor
   static constexpr bool LPT = true;   // items longest first
@@ -960,10 +956,6 @@ crk_status adjoint_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const
   Common c = make_common(plan, ws);
   cudaMemsetAsync(&c.hdr->queue[Q_A_C2], 0, 4 * sizeof(int32_t), st);
   if (n == 0) return CRK_OK;
-  if (plan->any_align() && !plan->aligned_built) {  // a tuned choice set after the build
-    crk_status s = align_impl(plan, st, ws);
-    if (s != CRK_OK) return s;
-  }
   R* ms = reinterpret_cast<R*>(ws + Ly.ms);
   R* rec_ab = reinterpret_cast<R*>(ws + Ly.adj_ab);
   R* rec_a1 = reinterpret_cast<R*>(ws + Ly.adj_rec1);

@@ -66,8 +66,6 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   L.wlen_g = take(4 * NW);
   L.wlen_s = take(4 * NW);
   L.ell = take(4 * (size_t)L.cap);
-  L.ell_u = take(4 * (size_t)L.cap);
-  L.wlen_u = take(4 * NW + 4);
   L.rec_b1 = take(R * B1 * N);
   L.rec_b2 = take(R * B2 * N);
   L.rec_c1 = take(R * C1 * N);
@@ -487,22 +485,12 @@ crk_status crk_rates_adjoint(crk_plan* plan, crk_stream_t stream, void* ws, cons
   return s;
 }
 
-// the eight tuned sweeps in the order of crk_autotune's choice_out; the union
-// sweeps can walk the warp-aligned lists
-static const int kTuneQueues[8] = {Q_B1, Q_B2, Q_C1, Q_C2, Q_A_C2, Q_A_C1, Q_A_B2, Q_A_B1};
-static const bool kTuneAlignable[8] = {false, false, false, true, true, true, true, true};
-constexpr int kLaunchVariants = 9;  // register caps x load modes (launch_sweep)
-
-static void set_choice(Plan& P, int q, int c) {
-  P.variant[kTuneQueues[q]] = c % kLaunchVariants;
-  P.align[kTuneQueues[q]] = kTuneAlignable[q] && c >= kLaunchVariants;
-}
-
 crk_status crk_tune_set(crk_plan* plan, const int32_t* choice) {
   if (!plan || !choice) return CRK_EINVAL;
   for (int q = 0; q < 8; ++q)
     if (choice[q] < 0 || choice[q] >= CRK_TUNE_VARIANTS) return CRK_EINVAL;
-  for (int q = 0; q < 8; ++q) set_choice(plan->impl, q, choice[q]);
+  static const int queues[8] = {Q_B1, Q_B2, Q_C1, Q_C2, Q_A_C2, Q_A_C1, Q_A_B2, Q_A_B1};
+  for (int q = 0; q < 8; ++q) plan->impl.variant[queues[q]] = choice[q];
   return CRK_OK;
 }
 
@@ -529,6 +517,7 @@ crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const voi
   void* gh = out + R * 11 * N;
   static const char* names[8] = {"b1_volume", "b2_moments", "c1_density", "c2_rates",
                                  "adj_c2",    "adj_c1",     "adj_b2",     "adj_b1"};
+  static const int queues[8] = {Q_B1, Q_B2, Q_C1, Q_C2, Q_A_C2, Q_A_C1, Q_A_B2, Q_A_B1};
   double tsum[8][CRK_TUNE_VARIANTS] = {};
   const bool was_timing = P.timing;
   auto run = [&]() -> crk_status {
@@ -561,8 +550,7 @@ crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const voi
     return r;
   };
   for (int k = 0; k < CRK_TUNE_VARIANTS; ++k) {
-    for (int q = 0; q < 8; ++q) set_choice(P, q, k);
-    if (k >= kLaunchVariants && !P.aligned_built && (s = align_impl(&P, st, w)) != CRK_OK) break;
+    for (int q = 0; q < 8; ++q) P.variant[queues[q]] = k;
     P.timing = false;
     if ((s = run()) != CRK_OK) break;
     for (int r = 0; r < repeats; ++r) {
@@ -574,8 +562,7 @@ crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const voi
       if ((s = crk_timing_read(plan, kt, Plan::kMaxTimed, &cnt)) != CRK_OK) break;
       for (int i = 0; i < cnt; ++i)
         for (int q = 0; q < 8; ++q)
-          if ((k < kLaunchVariants || kTuneAlignable[q]) && std::strcmp(kt[i].name, names[q]) == 0)
-            tsum[q][k] += kt[i].ms;
+          if (std::strcmp(kt[i].name, names[q]) == 0) tsum[q][k] += kt[i].ms;
     }
     if (s != CRK_OK) break;
   }
@@ -586,7 +573,7 @@ crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const voi
     for (int k = 1; k < CRK_TUNE_VARIANTS; ++k)
       if (tsum[q][k] > 0 && tsum[q][k] < tsum[q][best]) best = k;
     if (s != CRK_OK || (q >= 4 && !adj)) best = 0;
-    set_choice(P, q, best);
+    P.variant[queues[q]] = best;
     if (choice_out) choice_out[q] = best;
     if (ms_out)
       for (int k = 0; k < CRK_TUNE_VARIANTS; ++k)

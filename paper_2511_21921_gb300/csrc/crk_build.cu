@@ -873,152 +873,6 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
 }
 
 // ---------------------------------------------------------------------------
-// Warp-aligned union lists.  In a union sweep each lane of a warp walks its
-// own list and gathers the neighbor's record; the 32 lanes of a warp
-// (32 Morton-consecutive particles) share most neighbors -- each distinct
-// neighbor appears in about eight of the lanes' lists -- but at different list
-// positions, so every step of the walk requests up to 32 different records.
-// Here the lists of each warp are rescheduled so that lanes sharing a neighbor
-// take it in the same step: a load of one address by several lanes is served
-// once, which cuts the scattered requests per step several-fold.  Schedule:
-// the warp's distinct neighbors (a hash table in shared memory, with the lanes
-// that hold each as gather and scatter bit masks) in decreasing order of the
-// number of lanes that hold them, each placed in the earliest step where all
-// its lanes are free; steps are capped at the warp's longest list, and a
-// neighbor whose lanes have no common free step is placed lane by lane (a
-// lane with k entries always finds a free step among the first k).  A warp
-// whose distinct set does not fit the table keeps its lists in list order.
-// Steps where a lane has nothing hold kSentinel.  Each lane's entries are the
-// same as in ell, so every sum gets the same terms; only their order changes.
-// ---------------------------------------------------------------------------
-constexpr int kAlignHash = 1024;  // table slots per warp (distinct neighbors of 32 particles)
-constexpr int kAlignFill = 768;   // at most this many distinct neighbors are aligned
-
-__device__ __forceinline__ uint32_t align_hash(uint32_t j) {
-  return (j * 2654435761u) >> (32 - 10);  // 10 bits: kAlignHash slots
-}
-
-__global__ void __launch_bounds__(32) k_align(const uint32_t* __restrict__ ell,
-                                              const int32_t* __restrict__ cnt_g,
-                                              const int32_t* __restrict__ cnt_s, int64_t n,
-                                              int64_t cap_pp, uint32_t* __restrict__ ell_u,
-                                              int32_t* __restrict__ wlen_u) {
-  static_assert(kAlignHash == 1 << 10, "hash width");
-  extern __shared__ uint32_t al_smem[];
-  int32_t* key = reinterpret_cast<int32_t*>(al_smem);        // [kAlignHash], -1 = empty
-  uint32_t* gm = al_smem + kAlignHash;                        // lanes with the gather flag
-  uint32_t* sm = gm + kAlignHash;                             // lanes with the scatter flag
-  uint16_t* ord = reinterpret_cast<uint16_t*>(sm + kAlignHash);  // slots by lane count
-  uint32_t* occ = reinterpret_cast<uint32_t*>(ord + kAlignHash);  // [cap_pp] lanes busy per step
-  __shared__ int32_t bucket[34];
-  const int lane = threadIdx.x;
-  const int64_t w = blockIdx.x;
-  const int64_t s = w * 32 + lane;
-  const bool live = s < n;
-  const int lg = live ? cnt_g[s] : 0, ls = live ? cnt_s[s] : 0;
-  const int tot = lg + ls;
-  const int L = __reduce_max_sync(kFull, tot);
-  const uint32_t* col = ell + w * cap_pp * 32 + lane;
-  uint32_t* out = ell_u + w * cap_pp * 32 + lane;
-  for (int t = lane; t < kAlignHash; t += 32) key[t] = -1, gm[t] = 0u, sm[t] = 0u;
-  for (int t = lane; t < L; t += 32) occ[t] = 0u;
-  if (lane < 34) bucket[lane] = 0;
-  __syncwarp();
-  // distinct neighbors with the lanes that hold them
-  bool over = false;
-  for (int k = 0; k < tot && !over; ++k) {
-    const int64_t slot = k < lg ? k : cap_pp - 1 - (k - lg);
-    const uint32_t e = col[slot * 32];
-    const int32_t j = (int32_t)(e & kIdxMask);
-    uint32_t h = align_hash((uint32_t)j);
-    int probes = 0;
-    for (;;) {
-      const int32_t old = atomicCAS(&key[h], -1, j);
-      if (old == -1 || old == j) break;
-      h = (h + 1) & (kAlignHash - 1);
-      if (++probes >= kAlignHash) { over = true; break; }
-    }
-    if (over) break;
-    if (e & kGatherBit) atomicOr(&gm[h], 1u << lane);
-    if (e & kScatterBit) atomicOr(&sm[h], 1u << lane);
-  }
-  __syncwarp();
-  // count the distinct neighbors per number of holding lanes
-  int nd = 0;
-  for (int t = lane; t < kAlignHash; t += 32) {
-    if (key[t] >= 0) {
-      atomicAdd(&bucket[32 - __popc(gm[t] | sm[t])], 1);  // most lanes first
-      ++nd;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) nd += __shfl_xor_sync(kFull, nd, o);
-  over = __any_sync(kFull, over) || nd > kAlignFill;
-  __syncwarp();
-  if (over) {
-    // list order (the lists of ell, front part then back part)
-    for (int k = 0; k < L; ++k) {
-      uint32_t e = kSentinel;
-      if (k < tot) e = col[(int64_t)(k < lg ? k : cap_pp - 1 - (k - lg)) * 32];
-      out[(int64_t)k * 32] = e;
-    }
-    if (lane == 0) wlen_u[w] = L;
-    return;
-  }
-  if (lane == 0) {
-    int run = 0;
-    for (int b = 0; b < 33; ++b) {
-      const int c = bucket[b];
-      bucket[b] = run;
-      run += c;
-    }
-  }
-  __syncwarp();
-  for (int t = lane; t < kAlignHash; t += 32)
-    if (key[t] >= 0) ord[atomicAdd(&bucket[32 - __popc(gm[t] | sm[t])], 1)] = (uint16_t)t;
-  for (int k = 0; k < L; ++k) out[(int64_t)k * 32] = kSentinel;
-  __syncwarp();
-  // place every neighbor: the earliest step where all its lanes are free
-  for (int d = 0; d < nd; ++d) {
-    const int t0 = ord[d];
-    const uint32_t g = gm[t0], sc = sm[t0], m = g | sc;
-    const uint32_t j = (uint32_t)key[t0];
-    int step = -1;
-    for (int base = 0; base < L; base += 32) {
-      const int t = base + lane;
-      const bool fr = t < L && (occ[t] & m) == 0u;
-      const unsigned b = __ballot_sync(kFull, fr);
-      if (b) {
-        step = base + __ffs(b) - 1;
-        break;
-      }
-    }
-    const bool mine = (m >> lane) & 1u;
-    const uint32_t e = j | (((g >> lane) & 1u) ? kGatherBit : 0u) |
-                       (((sc >> lane) & 1u) ? kScatterBit : 0u);
-    if (step >= 0) {
-      if (lane == 0) occ[step] |= m;
-      if (mine) out[(int64_t)step * 32] = e;
-    } else if (mine) {
-      // no common free step: each lane takes its own earliest free one
-      for (int t = 0; t < L; ++t) {
-        if (!((occ[t] >> lane) & 1u)) {
-          atomicOr(&occ[t], 1u << lane);
-          out[(int64_t)t * 32] = e;
-          break;
-        }
-      }
-    }
-    __syncwarp();
-  }
-  if (lane == 0) wlen_u[w] = L;
-}
-
-size_t align_smem_bytes(int64_t cap_pp) {
-  return (size_t)kAlignHash * (4 + 4 + 4 + 2) + 4 * (size_t)cap_pp;
-}
-
-// ---------------------------------------------------------------------------
 // neighbor sets as CSR in caller order (inspection / tests)
 // ---------------------------------------------------------------------------
 __global__ void k_csr_counts(const int32_t* __restrict__ perm, const int32_t* __restrict__ cg,
@@ -1242,32 +1096,6 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
     k_item_sort<<<1, kLptThreads, 0, st>>>(seq_cost, Ly.nw,
                                            reinterpret_cast<int32_t*>(ws + Ly.seq_order));
   }
-  ph_lists.end();
-  plan->aligned_built = false;
-  if (plan->any_align()) {
-    crk_status a = align_impl(plan, st, ws);
-    if (a != CRK_OK) return a;
-  }
-  return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
-}
-
-crk_status align_impl(Plan* plan, cudaStream_t st, char* ws) {
-  const Layout& Ly = plan->ly;
-  if (Ly.n == 0) {
-    plan->aligned_built = true;
-    return CRK_OK;
-  }
-  const size_t smem = align_smem_bytes(Ly.cap_pp);
-  if (smem > 200 * 1024) return CRK_ENOMEM;  // list capacity too large to align
-  Phase ph(plan, st, "build.align", 1);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute((const void*)k_align, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-  k_align<<<(unsigned)Ly.nw, 32, smem, st>>>(
-      reinterpret_cast<const uint32_t*>(ws + Ly.ell), reinterpret_cast<const int32_t*>(ws + Ly.cnt_g),
-      reinterpret_cast<const int32_t*>(ws + Ly.cnt_s), Ly.n, Ly.cap_pp,
-      reinterpret_cast<uint32_t*>(ws + Ly.ell_u), reinterpret_cast<int32_t*>(ws + Ly.wlen_u));
-  plan->aligned_built = true;
   return cudaGetLastError() == cudaSuccess ? CRK_OK : CRK_ECUDA;
 }
 

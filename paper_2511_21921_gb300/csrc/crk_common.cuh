@@ -287,9 +287,6 @@ struct Layout {
   // and one 64-byte record per tree node (bounds, h_max, box range, children)
   size_t p4 = 0, nrec = 0;
   size_t cnt_g = 0, cnt_s = 0, wlen_g = 0, wlen_s = 0, ell = 0;
-  // union lists with the 32 lanes of a warp aligned on shared neighbors (same
-  // layout as ell; kSentinel where a lane has no entry) and their step counts
-  size_t ell_u = 0, wlen_u = 0;
   size_t rec_b1 = 0, rec_b2 = 0, rec_c1 = 0, rec_c2 = 0, coef = 0, Vs = 0, rhos = 0;
   size_t gvs = 0, Ds = 0;
   // active-set evaluation: sorted flags, scan scratch, compacted work lists

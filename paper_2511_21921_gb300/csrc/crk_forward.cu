@@ -40,7 +40,6 @@ template <class R> struct PassB1 {
   static constexpr int BLOCK = 256;
   static constexpr int MB0 = 1, MB1 = 1, MB2 = 1;  // resident-block variants
   static constexpr int QUEUE = Q_B1;
-  static constexpr bool ALIGNABLE = false;  // union sweep that can walk the aligned lists
   using Real = R;
   static constexpr int SW0 = Rec<R>::B1, SW1 = 0;  // words staged per neighbor
   static constexpr bool LPT = false;  // queue order (longest first gained nothing here)
@@ -116,7 +115,6 @@ template <class R> struct PassB2 {
   static constexpr int BLOCK = 256;
   static constexpr int MB0 = 1, MB1 = 3, MB2 = 4;  // resident-block variants
   static constexpr int QUEUE = Q_B2;
-  static constexpr bool ALIGNABLE = false;  // union sweep that can walk the aligned lists
   using Real = R;
   static constexpr int SW0 = Rec<R>::B2, SW1 = 0;  // words staged per neighbor
   static constexpr bool LPT = false;  // queue order (longest first gained nothing here)
@@ -240,7 +238,6 @@ template <class R> struct PassC1 {
   static constexpr int BLOCK = 256;
   static constexpr int MB0 = 1, MB1 = 4, MB2 = 5;  // resident-block variants
   static constexpr int QUEUE = Q_C1;
-  static constexpr bool ALIGNABLE = false;  // union sweep that can walk the aligned lists
   using Real = R;
   static constexpr int SW0 = Rec<R>::C1, SW1 = 0;  // words staged per neighbor
   static constexpr bool LPT = false;  // queue order (longest first gained nothing here)
@@ -370,7 +367,6 @@ template <class R, bool VAR = false> struct PassC2 {
   static constexpr int BLOCK = 128;
   static constexpr int MB0 = 2, MB1 = 3, MB2 = 4;  // resident-block variants
   static constexpr int QUEUE = Q_C2;
-  static constexpr bool ALIGNABLE = true;  // union sweep that can walk the aligned lists
   using Real = R;
   static constexpr int SW0 = Rec<R>::C2, SW1 = 0;  // words staged per neighbor
   static constexpr bool LPT = true;   // items longest first
@@ -517,10 +513,6 @@ crk_status rates_impl(Plan* plan, cudaStream_t st, char* ws, const R* v, const R
                               (R)p.Cq,
                               (R)p.relax_dt};
   launch_sweep<PassC1<R>>(plan, st, a1, "c1_density");
-  if (plan->any_align() && !plan->aligned_built) {  // a tuned choice set after the build
-    crk_status s = align_impl(plan, st, ws);
-    if (s != CRK_OK) return s;
-  }
   if (do_c2) {
     typename PassC2<R>::Args a2{c, rec_c2, reinterpret_cast<const R*>(ws + Ly.ms), us, dvdt,
                                 dudt, make_av<R>(p)};

@@ -35,15 +35,6 @@ struct Plan {
   int32_t nb = 0;
   Tuning tune[16];
   int variant[16] = {};  // launch variant per sweep: v % 3 -> MB0..MB2, v / 3 -> load mode
-  // union sweeps that walk the warp-aligned lists (per sweep queue), and
-  // whether the workspace holds them for the current build
-  bool align[16] = {};
-  bool aligned_built = false;
-  bool any_align() const {
-    for (int q = 0; q < 16; ++q)
-      if (align[q]) return true;
-    return false;
-  }
   // instrumentation
   long long launches = 0;
   bool timing = false;
@@ -86,9 +77,6 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
                            const R* h);
 crk_status neighbors_csr_impl(Plan* plan, cudaStream_t st, char* ws, int32_t mode,
                               int64_t* row_ptr, int32_t* col, int64_t cap, int64_t* nnz);
-// warp-aligned union lists of the current build (crk_build.cu)
-crk_status align_impl(Plan* plan, cudaStream_t st, char* ws);
-size_t align_smem_bytes(int64_t cap_pp);
 
 template <class R>
 crk_status moments_impl(Plan* plan, cudaStream_t st, char* ws, const R* m, R* V_out, R* coef_out);

@@ -37,12 +37,6 @@ struct Common {
   // gas and wind the volume sweep writes
   const uint8_t* spec = nullptr;
   void* Vgws = nullptr;
-  // warp-aligned union lists (see k_align) and their step counts per warp;
-  // set per launch: this union sweep walks them (warps of 32 consecutive
-  // particles, entries kSentinel where a lane has nothing in a step)
-  const uint32_t* ell_u = nullptr;
-  const int32_t* wlen_u = nullptr;
-  bool use_align = false;
 };
 
 // Ask L1 for the cache lines of neighbor j's record (base + j*bytes, `bytes`
@@ -75,8 +69,6 @@ inline Common make_common(const Plan* plan, char* ws) {
   c.seq_order = reinterpret_cast<const int32_t*>(ws + Ly.seq_order);
   c.n_bal = &c.hdr->n_all;
   c.Vgws = ws + Ly.Vgws;
-  c.ell_u = reinterpret_cast<const uint32_t*>(ws + Ly.ell_u);
-  c.wlen_u = reinterpret_cast<const int32_t*>(ws + Ly.wlen_u);
   return c;
 }
 
@@ -168,9 +160,7 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
   const int lane = threadIdx.x & 31;
   int32_t* q = &a.c.hdr->queue[P::QUEUE];
   extern __shared__ float4 ring[];
-  // union sweeps on the warp-aligned lists take warps of consecutive particles
-  const bool aligned = P::ALIGNABLE && a.c.use_align && !a.c.items;
-  const int32_t* its = a.c.items ? a.c.items : ((P::BALANCE && !aligned) ? a.c.bal : nullptr);
+  const int32_t* its = a.c.items ? a.c.items : (P::BALANCE ? a.c.bal : nullptr);
   const int64_t nlist = its ? (int64_t)*(a.c.items ? a.c.n_items : a.c.n_bal) : 0;
   const int64_t nwork = its ? (nlist + 31) / 32 : a.c.nw;
   for (;;) {
@@ -179,8 +169,7 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
     w = __shfl_sync(kFull, w, 0);
     if (w >= nwork) break;
     // the item this warp takes (items of consecutive particles may be reordered)
-    const int64_t wi =
-        (P::LPT && (!P::BALANCE || aligned) && a.c.lpt && !a.c.items) ? a.c.seq_order[w] : w;
+    const int64_t wi = (P::LPT && !P::BALANCE && a.c.lpt && !a.c.items) ? a.c.seq_order[w] : w;
     int64_t s = wi * 32 + lane;
     bool live = s < a.c.n;
     if (its) {
@@ -196,40 +185,33 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
       lg = a.c.cnt_g[s];
       ls = P::GATHER ? 0 : a.c.cnt_s[s];
     }
-    // the particle's own list column (warp-interleaved by sorted index), or
-    // the lane's column of the warp's aligned lists
+    // the particle's own list column (warp-interleaved by sorted index)
     const uint32_t* col = a.c.ell + (s >> 5) * a.c.cap_pp * 32 + (s & 31);
-    const uint32_t* colu = a.c.ell_u + wi * a.c.cap_pp * 32 + lane;
-    // entry k of this lane's union walk, kSentinel where it has none (the
-    // lists' gather part, then the scatter-only part; or the aligned steps)
-    const int tot = lg + ls;
-    const int wmax_u = aligned ? a.c.wlen_u[wi] : __reduce_max_sync(kFull, tot);
-    auto union_entry = [&](int k) -> uint32_t {
-      if (aligned) return k < wmax_u ? __ldg(colu + (int64_t)k * 32) : kSentinel;
-      if (k >= tot) return kSentinel;
-      const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
-      return __ldg(col + slot * 32);
-    };
     using Real = typename P::Real;
     if constexpr (STG) {
       // union list (gather part, then scatter-only part) through the ring
-      const int wmax = wmax_u;
+      const int tot = lg + ls;
+      const int wmax = __reduce_max_sync(kFull, tot);
+      auto entry = [&](int k) -> uint32_t {
+        const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
+        return __ldg(col + slot * 32);
+      };
       // a bad entry (bounds-checked build only) is redirected to the particle itself
       auto safe = [&](uint32_t e) -> uint32_t {
-        return (e == kSentinel || index_ok(a.c.hdr, e & kIdxMask, a.c.n)) ? e : (uint32_t)s;
+        return index_ok(a.c.hdr, e & kIdxMask, a.c.n) ? e : (uint32_t)s;
       };
-      uint32_t e_next = safe(union_entry(0));
-      if (e_next != kSentinel) Stage<P>::issue(a, ring, 0, e_next & kIdxMask);
+      uint32_t e_next = tot > 0 ? safe(entry(0)) : 0u;
+      if (tot > 0) Stage<P>::issue(a, ring, 0, e_next & kIdxMask);
       cp_async_commit();
-      uint32_t e_after = safe(union_entry(1));
+      uint32_t e_after = tot > 1 ? safe(entry(1)) : 0u;
       for (int k = 0; k < wmax; ++k) {
         const uint32_t e = e_next;
         e_next = e_after;
-        if (e_next != kSentinel) Stage<P>::issue(a, ring, (k + 1) & 1, e_next & kIdxMask);
+        if (k + 1 < tot) Stage<P>::issue(a, ring, (k + 1) & 1, e_next & kIdxMask);
         cp_async_commit();
-        e_after = safe(union_entry(k + 2));
+        e_after = k + 2 < tot ? safe(entry(k + 2)) : 0u;
         cp_async_wait<1>();
-        if (e != kSentinel) {
+        if (k < tot) {
           Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
           Stage<P>::read(ring, k & 1, r0, r1);
           P::pair_s(a, st, r0, r1, e & kIdxMask, e);
@@ -241,13 +223,18 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
       // double buffer: the record of entry k+1 is loaded while the pair of
       // entry k is evaluated, and the list entry one further ahead.  Unrolled
       // by two so that the buffers alternate without register copies.
-      const int wmax = P::GATHER && !its ? a.c.wlen_g[wi] : wmax_u;
-      auto raw = [&](int k) -> uint32_t { return union_entry(k); };
+      const int tot = lg + ls;
+      const int wmax = P::GATHER && !its ? a.c.wlen_g[wi] : __reduce_max_sync(kFull, tot);
+      auto raw = [&](int k) -> uint32_t {
+        if (k >= tot) return 0u;
+        const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
+        return __ldg(col + slot * 32);
+      };
       uint32_t enext = raw(0);
       auto fetch = [&](int k, uint32_t& e, bool& ok, Real* r0, Real* r1) {
         e = enext;
         enext = raw(k + 1);
-        ok = e != kSentinel && index_ok(a.c.hdr, e & kIdxMask, a.c.n);
+        ok = k < tot && index_ok(a.c.hdr, e & kIdxMask, a.c.n);
         if (ok) load_sources<P>(a, e & kIdxMask, r0, r1);
       };
       Real A0[P::SW0], A1[P::SW1 > 0 ? P::SW1 : 1], B0[P::SW0], B1[P::SW1 > 0 ? P::SW1 : 1];
@@ -277,19 +264,24 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
     } else {
       // gather part then scatter-only part as one list per lane, so the warp
       // runs to its longest union list rather than to the sum of the longest
-      // parts (or the warp's aligned steps)
-      const int wmax = wmax_u;
+      // parts
+      const int tot = lg + ls;
+      const int wmax = __reduce_max_sync(kFull, tot);
       const int pf = a.c.pf;
       for (int k = 0; k < wmax; ++k) {
-        if (pf) {
-          const uint32_t ep = union_entry(k + pf);
-          if (ep != kSentinel) prefetch_sources<P>(a, ep & kIdxMask);
+        if (pf && k + pf < tot) {
+          const int kp = k + pf;
+          const int64_t sp = kp < lg ? kp : a.c.cap_pp - 1 - (kp - lg);
+          prefetch_sources<P>(a, __ldg(col + sp * 32) & kIdxMask);
         }
-        const uint32_t e = union_entry(k);
-        if (e != kSentinel && index_ok(a.c.hdr, e & kIdxMask, a.c.n)) {
-          Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
-          load_sources<P>(a, e & kIdxMask, r0, r1);
-          P::pair_s(a, st, r0, r1, e & kIdxMask, e);
+        if (k < tot) {
+          const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
+          const uint32_t e = __ldg(col + slot * 32);
+          if (index_ok(a.c.hdr, e & kIdxMask, a.c.n)) {
+            Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
+            load_sources<P>(a, e & kIdxMask, r0, r1);
+            P::pair_s(a, st, r0, r1, e & kIdxMask, e);
+          }
         }
       }
     }
@@ -554,7 +546,6 @@ void launch_variant(Plan* plan, cudaStream_t st, const typename P::Args& a) {
   const int grid = sweep_grid(plan, fn, P::BLOCK, (int)smem);
   typename P::Args b = a;
   b.c.lpt = P::LPT && lpt_worthwhile(plan->ly.nw, (int64_t)grid * P::BLOCK / 32);
-  b.c.use_align = P::ALIGNABLE && plan->align[P::QUEUE] && plan->aligned_built;
   k_sweep<P, MB, MODE><<<grid, P::BLOCK, smem, st>>>(b);
 }
 
@@ -568,8 +559,7 @@ void launch_sweep_plain(Plan* plan, cudaStream_t st, const typename P::Args& a, 
 
 // Variant v of a sweep: v % 3 picks the resident-block count (MB0..MB2),
 // v / 3 the mode (0 plain loads, 1 shared-memory ring, 2 register double
-// buffer); whether a union sweep walks the warp-aligned lists is the plan's
-// align flag of the sweep.
+// buffer).
 template <class P>
 void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const char* name) {
   const int v = plan->variant[P::QUEUE];
