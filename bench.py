@@ -46,12 +46,26 @@ WORKLOAD_DESCS = {
 # boxes above this size are timed on the CPU through a region sample
 REGION_SAMPLE_ABOVE = 1 << 21
 
-# Algorithmic flops per unit of each sweep (add/mul/div/sqrt/exp = 1, fused
-# multiply-add = 2), tallied from the expressions the kernels evaluate.  Units:
-# ordered union pairs for c2 and its adjoint; gather pairs for the others (the
-# adjoint b1/b2/c1 counts cover both roles a gather pair plays).
-FLOPS_PER_PAIR = {"b1_volume": 31, "b2_moments": 114, "c1_density": 117, "c2_rates": 253,
-                  "adj_c2": 654, "adj_c1": 511, "adj_b2": 458, "adj_b1": 93}
+# Algorithmic flops per unit of each sweep: the oracle's own operation count
+# (add, subtract, multiply, divide, sqrt, exp = 1; oracle.count_ops), per unit
+# of the sweep, averaged over the 32^3 clustered box (the 64^3 box gives the
+# same to 0.3 %).  Units: ordered union pairs for the rates and their adjoint,
+# ordered gather pairs (j != i) for the others.  A forward sweep counts the
+# operations of its stage of the oracle (per-particle work included); the
+# adjoint sweep of a stage counts that stage's forward operations, which it
+# recomputes, plus the derivative operations of the oracle's forward-mode
+# differentiation of the stage (one tangent).  tests/test_flop_counts.py
+# recounts them.
+FLOPS_RECOMPUTE = {"b1_volume": 30, "b2_moments": 215, "c1_density": 131, "c2_rates": 317,
+                   "adj_c2": 317, "adj_c1": 131, "adj_b2": 215, "adj_b1": 30}
+FLOPS_DERIVATIVE = {"b1_volume": 0, "b2_moments": 0, "c1_density": 0, "c2_rates": 0,
+                    "adj_c2": 720, "adj_c1": 302, "adj_b2": 505, "adj_b1": 64}
+FLOPS_PER_PAIR = {k: FLOPS_RECOMPUTE[k] + FLOPS_DERIVATIVE[k] for k in FLOPS_RECOMPUTE}
+# The kernels' own tally of the expressions they evaluate (reduced moment
+# sums, intermediates shared between the forward recompute and the reverse):
+# lower than the oracle's count; reported beside it.
+FLOPS_KERNEL_TALLY = {"b1_volume": 31, "b2_moments": 114, "c1_density": 117, "c2_rates": 253,
+                      "adj_c2": 654, "adj_c1": 511, "adj_b2": 458, "adj_b1": 93}
 UNIT_OF = {"b1_volume": "gather", "b2_moments": "gather", "c1_density": "gather",
            "c2_rates": "union", "adj_c2": "union", "adj_c1": "gather", "adj_b2": "gather",
            "adj_b1": "gather"}
@@ -350,14 +364,22 @@ def run_ours(args, rank, world, workload=None, light=False):
         achieved = FLOPS_PER_PAIR[dom] * units[UNIT_OF[dom]] / (kmean[dom] * 1e-3) / 1e12
         per_kernel = {k: round(FLOPS_PER_PAIR[k] * units[UNIT_OF[k]] / (kmean[k] * 1e-3) / 1e12, 3)
                       for k in kmean if k in FLOPS_PER_PAIR}
+        tally = FLOPS_KERNEL_TALLY[dom] * units[UNIT_OF[dom]] / (kmean[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                 "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
                 "traffic": profiled_traffic(dom, name),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                "flops_per_pair": FLOPS_PER_PAIR[dom], "pairs": units[UNIT_OF[dom]],
+                "flops_per_pair": FLOPS_PER_PAIR[dom],
+                "flops_per_pair_split": {"recompute": FLOPS_RECOMPUTE[dom],
+                                         "derivative": FLOPS_DERIVATIVE[dom]},
+                "flops_source": "the oracle's operation count of the formulas (oracle.count_ops)",
+                "pairs": units[UNIT_OF[dom]],
                 "kernel_ms": round(kmean[dom], 4),
                 "frac_of_measured_fp32": round(achieved / alu_fp32, 4) if alu_fp32 else None,
+                "kernel_tally": {"flops_per_pair": FLOPS_KERNEL_TALLY[dom],
+                                 "achieved": round(tally, 3),
+                                 "frac": round(tally / FP32_PEAK_TFLOPS, 4)},
                 "on_chip": profiled_limiter(dom, name)}
         return roof, per_kernel
 

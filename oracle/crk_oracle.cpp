@@ -89,6 +89,55 @@ inline double val(const Dual& a) { return a.v; }
 inline double tan_of(double) { return 0.0; }
 inline double tan_of(const Dual& a) { return a.d; }
 
+// ----------------------------------------------------------------------------
+// operation counting (the algorithmic flop counts of the benchmark): a value
+// type that counts every add, subtract, multiply, divide, square root and
+// exponential it performs (one each), and a dual number that counts the
+// operations on its value and on its tangent separately.  Comparisons and
+// selections count nothing.  The counters are per thread; counting runs on
+// one thread.
+// ----------------------------------------------------------------------------
+thread_local int64_t g_val_ops = 0, g_tan_ops = 0;
+struct Cnt {
+  double v;
+  Cnt() : v(0) {}
+  Cnt(double a) : v(a) {}
+};
+inline Cnt operator+(Cnt a, Cnt b) { ++g_val_ops; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { ++g_val_ops; return Cnt(a.v - b.v); }
+inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+inline Cnt operator*(Cnt a, Cnt b) { ++g_val_ops; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { ++g_val_ops; return Cnt(a.v / b.v); }
+inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
+inline Cnt& operator-=(Cnt& a, Cnt b) { a = a - b; return a; }
+inline Cnt& operator*=(Cnt& a, Cnt b) { a = a * b; return a; }
+inline Cnt sqrt(Cnt a) { ++g_val_ops; return Cnt(std::sqrt(a.v)); }
+inline Cnt exp(Cnt a) { ++g_val_ops; return Cnt(std::exp(a.v)); }
+inline double val(const Cnt& a) { return a.v; }
+inline double tan_of(const Cnt&) { return 0.0; }
+
+// a dual number counting value operations (as Cnt) and tangent operations:
+// d(a+b) 1, d(ab) 3, d(a/b) 3 (reusing the quotient), d sqrt 2, d exp 1
+struct CDual {
+  Dual x;
+  CDual() {}
+  CDual(double a) : x(a) {}
+  CDual(double a, double b) : x(a, b) {}
+  CDual(Dual d) : x(d) {}
+};
+inline CDual operator+(CDual a, CDual b) { ++g_val_ops; ++g_tan_ops; return CDual(a.x + b.x); }
+inline CDual operator-(CDual a, CDual b) { ++g_val_ops; ++g_tan_ops; return CDual(a.x - b.x); }
+inline CDual operator-(CDual a) { return CDual(-a.x); }
+inline CDual operator*(CDual a, CDual b) { ++g_val_ops; g_tan_ops += 3; return CDual(a.x * b.x); }
+inline CDual operator/(CDual a, CDual b) { ++g_val_ops; g_tan_ops += 3; return CDual(a.x / b.x); }
+inline CDual& operator+=(CDual& a, CDual b) { a = a + b; return a; }
+inline CDual& operator-=(CDual& a, CDual b) { a = a - b; return a; }
+inline CDual& operator*=(CDual& a, CDual b) { a = a * b; return a; }
+inline CDual sqrt(CDual a) { ++g_val_ops; g_tan_ops += 2; return CDual(sqrt(a.x)); }
+inline CDual exp(CDual a) { ++g_val_ops; g_tan_ops += 1; return CDual(exp(a.x)); }
+inline double val(const CDual& a) { return a.x.v; }
+inline double tan_of(const CDual& a) { return a.x.d; }
+
 template <class T> inline T tmax(T a, T b) { return val(a) >= val(b) ? a : b; }
 template <class T> inline T tmin(T a, T b) { return val(a) <= val(b) ? a : b; }
 template <class T> inline T tabs(T a) { return val(a) < 0 ? T(0) - a : a; }
@@ -721,6 +770,37 @@ void load_inputs<Dual>(Eval<Dual>& E, const double* x, const double* h, const do
   }
 }
 
+template <>
+void load_inputs<Cnt>(Eval<Cnt>& E, const double* x, const double* h, const double* m,
+                      const double* v, const double* u, const double*, const double*,
+                      const double*, const double*) {
+  int64_t n = E.n;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      E.x[a][i] = Cnt(x[a * n + i]);
+      E.v[a][i] = Cnt(v ? v[a * n + i] : 0.0);
+    }
+    E.h[i] = Cnt(h[i]);
+    E.m[i] = Cnt(m[i]);
+    E.u[i] = Cnt(u ? u[i] : 0.0);
+  }
+}
+template <>
+void load_inputs<CDual>(Eval<CDual>& E, const double* x, const double* h, const double* m,
+                        const double* v, const double* u, const double* tx, const double* th,
+                        const double* tv, const double* tu) {
+  int64_t n = E.n;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      E.x[a][i] = CDual(x[a * n + i], tx ? tx[a * n + i] : 0.0);
+      E.v[a][i] = CDual(v ? v[a * n + i] : 0.0, tv ? tv[a * n + i] : 0.0);
+    }
+    E.h[i] = CDual(h[i], th ? th[i] : 0.0);
+    E.m[i] = CDual(m[i], 0.0);
+    E.u[i] = CDual(u ? u[i] : 0.0, tu ? tu[i] : 0.0);
+  }
+}
+
 template <class T>
 int run(int64_t n, const double* x, const double* h, const double* m, const double* v,
         const double* u, double L, const oracle_params* p, const double* tx, const double* th,
@@ -980,6 +1060,38 @@ int oracle_forward_state(int64_t n, const double* x, const double* h, const doub
                          oracle_out* out) {
   return run_state(n, x, h, m, v, u, L, p, flags, V_state, coef_state, rho_state, gradv_state,
                    nthreads, out);
+}
+
+// Operation counts of a whole-box evaluation up to `stages` (1 volume, 2 +
+// coefficients, 3 + density and velocity gradient, 4 + rates) on one thread:
+// with derivative = 0 the plain evaluation (ops[0]: its operations), with
+// derivative = 1 the forward-mode derivative along (tx, tv, tu, th) (ops[0]:
+// operations on values, ops[1]: operations on tangents).  The differences
+// between consecutive stages, per pair of the stage's neighbor sets, are the
+// algorithmic flops per pair of the matching sweeps.
+int oracle_count_ops(int64_t n, const double* x, const double* h, const double* m,
+                     const double* v, const double* u, double L, const oracle_params* p,
+                     const double* tx, const double* tv, const double* tu, const double* th,
+                     int32_t stages, int32_t derivative, int64_t* ops) {
+  if (!ops) return EINVAL_;
+#ifdef _OPENMP
+  const int threads_before = omp_get_max_threads();
+#endif
+  g_val_ops = 0;
+  g_tan_ops = 0;
+  int rc;
+  if (derivative)
+    rc = run<CDual>(n, x, h, m, v, u, L, p, tx, th, tv, tu, n, nullptr, stages, 1, 1, nullptr,
+                    nullptr);
+  else
+    rc = run<Cnt>(n, x, h, m, v, u, L, p, nullptr, nullptr, nullptr, nullptr, n, nullptr, stages,
+                  1, 1, nullptr, nullptr);
+  ops[0] = g_val_ops;
+  ops[1] = g_tan_ops;
+#ifdef _OPENMP
+  omp_set_num_threads(threads_before);
+#endif
+  return rc;
 }
 
 // The kernel itself, for the quadrature and finite-difference pins.

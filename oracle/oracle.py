@@ -104,6 +104,10 @@ def _load():
                                              C.c_double, dp, dp, C.c_int64, dp]
             lib.oracle_kernel.restype = None
             lib.oracle_kernel.argtypes = [C.c_int64, dp, C.c_double, dp, dp, dp]
+            lib.oracle_count_ops.restype = C.c_int
+            lib.oracle_count_ops.argtypes = [C.c_int64, dp, dp, dp, dp, dp, C.c_double,
+                                             C.POINTER(OracleParams), dp, dp, dp, dp, C.c_int32,
+                                             C.c_int32, dp]
             lib.oracle_num_threads.restype = C.c_int
             _lib = lib
     return _lib
@@ -263,6 +267,27 @@ def jvp(x, h, m, v, u, L, tx=None, tv=None, tu=None, th=None, params=None, targe
     if rc not in (0, 6):
         raise ValueError(f"oracle_jvp: {STATUS.get(rc, rc)}")
     return arrs, tarrs
+
+
+def count_ops(x, h, m, v, u, L, stages, derivative=False, tx=None, tv=None, tu=None, th=None,
+              params=None):
+    """Operations of a whole-box evaluation up to ``stages`` (1..4) counted by
+    the oracle itself (add, subtract, multiply, divide, sqrt, exp = 1 each), on
+    one thread.  Returns (value operations, tangent operations); the tangent
+    count is 0 unless ``derivative`` (the forward-mode derivative along the
+    given tangents)."""
+    lib = _load()
+    n, x, h, m, v, u = _inputs(x, h, m, v, u)
+    p = params if params is not None else default_params()
+    t = [_f64(a, s) if a is not None else None
+         for a, s in ((tx, (3, n)), (tv, (3, n)), (tu, (n,)), (th, (n,)))]
+    ops = np.zeros(2, dtype=np.int64)
+    rc = lib.oracle_count_ops(n, _ptr(x), _ptr(h), _ptr(m), _ptr(v), _ptr(u), float(L), C.byref(p),
+                              _ptr(t[0]), _ptr(t[1]), _ptr(t[2]), _ptr(t[3]), int(stages),
+                              1 if derivative else 0, _ptr(ops))
+    if rc not in (0, 6):
+        raise ValueError(f"oracle_count_ops: {STATUS.get(rc, rc)}")
+    return int(ops[0]), int(ops[1])
 
 
 def neighbors(x, h, L=1.0, mode="gather", method="tree"):
