@@ -294,8 +294,12 @@ def run_ours(args, rank, world, workload=None, light=False):
         if with_adj:
             s.adjoint(src["v"], src["u"], src["ga"], src["gu"], recompute=False, out=grads)
 
-    tuned = s.autotune(dv["m"], dv["v"], dv["u"], dv["ga"] if with_adj else None,
-                       dv["gu"] if with_adj else None, repeats=3) if args.autotune else None
+    tuned = None
+    if args.tune:  # a stored autotuner choice (8 variants in the order of _lib.SWEEPS)
+        s.tune_set([int(c) for c in args.tune.split(",")])
+    elif args.autotune:
+        tuned = s.autotune(dv["m"], dv["v"], dv["u"], dv["ga"] if with_adj else None,
+                           dv["gu"] if with_adj else None, repeats=3)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -953,6 +957,10 @@ def main():
     ap.add_argument("--fwd-only", action="store_true")
     ap.add_argument("--no-graph", dest="graph", action="store_false", default=True)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false", default=True)
+    ap.add_argument("--tune", default="",
+                    help="set a stored autotuner choice instead of tuning: 8 comma-separated "
+                         "variants (volume, moments, density, rates, adjoint rates, adjoint "
+                         "density, adjoint moments, adjoint volume)")
     ap.add_argument("--prefetch", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-small", dest="small", action="store_false", default=True,
