@@ -74,10 +74,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 # kernel names of the sweeps as they appear in ncu captures (profiles/*.md)
-PROFILE_KERNEL = {"b1_volume": "PassB1<float>", "b2_moments": "PassB2<float>",
-                  "c1_density": "PassC1<float>", "c2_rates": "PassC2<float>",
-                  "adj_c2": "PassA2<float>", "adj_c1": "PassA1<float>", "adj_b2": "PassAB2<float>",
-                  "adj_b1": "PassAB1<float>"}
+PROFILE_KERNEL = {"b1_volume": "PassB1<float", "b2_moments": "PassB2<float",
+                  "c1_density": "PassC1<float", "c2_rates": "PassC2<float",
+                  "adj_c2": "PassA2<float", "adj_c1": "PassA1<float", "adj_b2": "PassAB2<float",
+                  "adj_b1": "PassAB1<float"}
 
 
 def _profile_of(kernel: str, workload: str, need=None):
