@@ -85,19 +85,20 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Staging ring of a sweep whose pass sets STAGED: every thread owns two slots
-// of SV 16-byte vectors each, laid out [slot][vector][thread] so that the
-// threads of a warp touch consecutive 16-byte words (no bank conflicts).  The
-// neighbor record of list entry k+1 is copied into one slot while the pair of
-// entry k is evaluated from the other, so the gather latency overlaps the
-// arithmetic instead of stalling it.  Each thread reads back only its own
-// slots, and every value it reads is consumed before the slot is refilled.
+// Staging ring of the record-ring load modes: every thread owns NS slots (two,
+// or the pass's DEEP) of SV 16-byte vectors each, laid out [slot][vector]
+// [thread] so that the threads of a warp touch consecutive 16-byte words (no
+// bank conflicts).  The neighbor records of list entries k+1 .. k+NS-1 are in
+// flight while the pair of entry k is evaluated from its slot, so the gather
+// latency overlaps the arithmetic instead of stalling it.  Each thread reads
+// back only its own slots, and every value it reads is consumed before the
+// slot is refilled.
 template <class P> struct Stage {
   using R = typename P::Real;
   static constexpr int V0 = P::SW0 * (int)sizeof(R) / 16;  // vectors of source 0
   static constexpr int V1 = P::SW1 * (int)sizeof(R) / 16;  // vectors of source 1
   static constexpr int SV = V0 + V1;
-  static constexpr size_t bytes = (size_t)2 * SV * P::BLOCK * 16;
+  static constexpr size_t bytes(int ns) { return (size_t)ns * SV * P::BLOCK * 16; }
   __device__ static void issue(const typename P::Args& a, float4* ring, int slot, uint32_t j) {
     const int t = threadIdx.x;
     const float4* g0 = reinterpret_cast<const float4*>(P::src0(a)) + (size_t)j * V0;
@@ -144,19 +145,27 @@ constexpr int sweep_regs(int block, int minb) {
   return r > 255 ? 255 : r;
 }
 
+// Ring slots and register buffers of a load mode (see k_sweep).
+template <class P, int MODE> constexpr int mode_depth() {
+  return (MODE == 3 || MODE == 4) ? P::DEEP : 2;
+}
+
 // Persistent sweep: warps pull 32-particle work items from an atomic queue --
 // 32 consecutive sorted particles, or 32 entries of a work list (the active
 // set's compacted list, or for passes with BALANCE the build's list ordered by
 // union-list length).  MINB (minimum resident blocks per SM) sets the register
 // cap and MODE how the neighbor records reach the pair arithmetic: 0 loaded
-// from global memory when the pair is evaluated, 1 copied ahead through the
-// shared-memory ring, 2 loaded one entry ahead into a register double buffer.
+// from global memory when the pair is evaluated, 1 copied one entry ahead
+// through the shared-memory ring, 2 loaded one entry ahead into a register
+// double buffer, 3 and 4 the same two with DEEP - 1 entries in flight (the
+// light passes, whose few flops per pair cannot cover one gather's latency).
 // Each pass is compiled for three MINB values in each mode and the autotuner
-// picks one of the nine per plan.
+// picks one of the fifteen per plan.
 template <class P, int MINB, int MODE>
 __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MINB))
     k_sweep(const typename P::Args a) {
-  constexpr bool STG = MODE == 1;
+  constexpr bool STG = MODE == 1 || MODE == 3;
+  constexpr int NS = mode_depth<P, MODE>();
   const int lane = threadIdx.x & 31;
   int32_t* q = &a.c.hdr->queue[P::QUEUE];
   extern __shared__ float4 ring[];
@@ -200,24 +209,89 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
       auto safe = [&](uint32_t e) -> uint32_t {
         return index_ok(a.c.hdr, e & kIdxMask, a.c.n) ? e : (uint32_t)s;
       };
-      uint32_t e_next = tot > 0 ? safe(entry(0)) : 0u;
-      if (tot > 0) Stage<P>::issue(a, ring, 0, e_next & kIdxMask);
-      cp_async_commit();
-      uint32_t e_after = tot > 1 ? safe(entry(1)) : 0u;
-      for (int k = 0; k < wmax; ++k) {
-        const uint32_t e = e_next;
-        e_next = e_after;
-        if (k + 1 < tot) Stage<P>::issue(a, ring, (k + 1) & 1, e_next & kIdxMask);
+      if constexpr (NS == 2) {
+        uint32_t e_next = tot > 0 ? safe(entry(0)) : 0u;
+        if (tot > 0) Stage<P>::issue(a, ring, 0, e_next & kIdxMask);
         cp_async_commit();
-        e_after = k + 2 < tot ? safe(entry(k + 2)) : 0u;
-        cp_async_wait<1>();
-        if (k < tot) {
-          Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
-          Stage<P>::read(ring, k & 1, r0, r1);
-          P::pair_s(a, st, r0, r1, e & kIdxMask, e);
+        uint32_t e_after = tot > 1 ? safe(entry(1)) : 0u;
+        for (int k = 0; k < wmax; ++k) {
+          const uint32_t e = e_next;
+          e_next = e_after;
+          if (k + 1 < tot) Stage<P>::issue(a, ring, (k + 1) & 1, e_next & kIdxMask);
+          cp_async_commit();
+          e_after = k + 2 < tot ? safe(entry(k + 2)) : 0u;
+          cp_async_wait<1>();
+          if (k < tot) {
+            Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
+            Stage<P>::read(ring, k & 1, r0, r1);
+            P::pair_s(a, st, r0, r1, e & kIdxMask, e);
+          }
+        }
+      } else {
+        // NS slots: entry k lives in slot k % NS and its copy is commit group
+        // k; the loop is unrolled by NS so that slots and entries are static.
+        uint32_t ent[NS];
+#pragma unroll
+        for (int i = 0; i < NS - 1; ++i) {
+          ent[i] = i < tot ? safe(entry(i)) : 0u;
+          if (i < tot) Stage<P>::issue(a, ring, i, ent[i] & kIdxMask);
+          cp_async_commit();
+        }
+        uint32_t e_ahead = NS - 1 < tot ? safe(entry(NS - 1)) : 0u;
+        for (int k0 = 0; k0 < wmax; k0 += NS) {
+#pragma unroll
+          for (int d = 0; d < NS; ++d) {
+            const int k = k0 + d;
+            const int sl = (d + NS - 1) % NS;  // the slot of entry k + NS - 1
+            ent[sl] = e_ahead;
+            if (k + NS - 1 < tot) Stage<P>::issue(a, ring, sl, e_ahead & kIdxMask);
+            cp_async_commit();
+            e_ahead = k + NS < tot ? safe(entry(k + NS)) : 0u;
+            cp_async_wait<NS - 1>();  // groups 0 .. k have landed
+            if (k < tot) {
+              Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
+              Stage<P>::read(ring, d, r0, r1);
+              P::pair_s(a, st, r0, r1, ent[d] & kIdxMask, ent[d]);
+            }
+          }
         }
       }
       cp_async_wait<0>();
+    } else if constexpr (MODE == 4) {
+      // DEEP register buffers: the records of entries k+1 .. k+DEEP-1 are in
+      // flight while the pair of entry k is evaluated, and each list entry is
+      // read DEEP steps before its record.  Unrolled by DEEP so that the
+      // buffers rotate without register copies.
+      constexpr int D = NS;
+      const int tot = lg + ls;
+      const int wmax = P::GATHER && !its ? a.c.wlen_g[wi] : __reduce_max_sync(kFull, tot);
+      auto raw = [&](int k) -> uint32_t {
+        if (k >= tot) return 0u;
+        const int64_t slot = k < lg ? k : a.c.cap_pp - 1 - (k - lg);
+        return __ldg(col + slot * 32);
+      };
+      Real b0[D][P::SW0], b1[D][P::SW1 > 0 ? P::SW1 : 1];
+      uint32_t eb[D], en[D];
+      bool ok[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        eb[i] = raw(i);
+        ok[i] = i < tot && index_ok(a.c.hdr, eb[i] & kIdxMask, a.c.n);
+        if (ok[i]) load_sources<P>(a, eb[i] & kIdxMask, b0[i], b1[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) en[i] = raw(D + i);
+      for (int k0 = 0; k0 < wmax; k0 += D) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const int k = k0 + d;
+          if (ok[d]) P::pair_s(a, st, b0[d], b1[d], eb[d] & kIdxMask, eb[d]);
+          eb[d] = en[d];  // entry k + D
+          ok[d] = k + D < tot && index_ok(a.c.hdr, eb[d] & kIdxMask, a.c.n);
+          if (ok[d]) load_sources<P>(a, eb[d] & kIdxMask, b0[d], b1[d]);
+          en[d] = raw(k + 2 * D);
+        }
+      }
     } else if constexpr (MODE == 2) {
       // the gather part (gather passes) or the union list, with a register
       // double buffer: the record of entry k+1 is loaded while the pair of
@@ -539,7 +613,7 @@ template <class R> struct PairC2 {
 
 template <class P, int MB, int MODE>
 void launch_variant(Plan* plan, cudaStream_t st, const typename P::Args& a) {
-  const size_t smem = MODE == 1 ? Stage<P>::bytes : 0;
+  const size_t smem = (MODE == 1 || MODE == 3) ? Stage<P>::bytes(mode_depth<P, MODE>()) : 0;
   const void* fn = (const void*)k_sweep<P, MB, MODE>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -559,7 +633,7 @@ void launch_sweep_plain(Plan* plan, cudaStream_t st, const typename P::Args& a, 
 
 // Variant v of a sweep: v % 3 picks the resident-block count (MB0..MB2),
 // v / 3 the mode (0 plain loads, 1 shared-memory ring, 2 register double
-// buffer).
+// buffer, 3 deep ring, 4 deep register buffers).
 template <class P>
 void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const char* name) {
   const int v = plan->variant[P::QUEUE];
@@ -573,6 +647,12 @@ void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const 
     case 6: launch_variant<P, P::MB0, 2>(plan, st, a); break;
     case 7: launch_variant<P, P::MB1, 2>(plan, st, a); break;
     case 8: launch_variant<P, P::MB2, 2>(plan, st, a); break;
+    case 9: launch_variant<P, P::MB0, 3>(plan, st, a); break;
+    case 10: launch_variant<P, P::MB1, 3>(plan, st, a); break;
+    case 11: launch_variant<P, P::MB2, 3>(plan, st, a); break;
+    case 12: launch_variant<P, P::MB0, 4>(plan, st, a); break;
+    case 13: launch_variant<P, P::MB1, 4>(plan, st, a); break;
+    case 14: launch_variant<P, P::MB2, 4>(plan, st, a); break;
     default: launch_variant<P, P::MB0, 0>(plan, st, a); break;
   }
 }

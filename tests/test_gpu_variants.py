@@ -1,6 +1,7 @@
 """Every compiled launch variant of the eight neighbor sweeps -- three register
-caps times three ways of bringing the neighbor records to the pair arithmetic
-(plain loads, shared-memory ring, register double buffer) -- gives the oracle's
+caps times five ways of bringing the neighbor records to the pair arithmetic
+(plain loads, shared-memory ring, register double buffer, and the ring and the
+register buffers with several records in flight) -- gives the oracle's
 results: the forward fields and rates element by element, the adjoint through
 a dot test against the oracle's forward-mode derivative, and the active-set
 path, whose sweeps walk a compacted work list instead of consecutive warps."""
