@@ -631,7 +631,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
     // predicate r^2 < max(h_i^2, h_j^2), widened by the rounding band; only
     // the hits (a few per stage) are then emitted, in candidate order, with the
     // same r^2 recomputed to tell gather from scatter-only and the pairs
-    // within the band decided exactly.
+    // within the band decided exactly.  The emit loop diverges (a warp runs
+    // it as often as its busiest lane has hits), so it takes two hits per
+    // iteration: their loads and decisions overlap and the loop runs about
+    // half as many times.
     auto test_stage = [&]() {
       uint32_t hit = 0u;
 #pragma unroll
@@ -641,26 +644,41 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         hit |= (r2 < fmaxf(hi2w, t.w) ? 1u : 0u) << k;
       }
-      while (hit) {
-        const int k = __ffs(hit) - 1;
-        hit &= hit - 1u;
-        const int32_t j = sj[wib][k];
-        if (j == s) continue;
+      auto decide = [&](int k, int32_t& j, bool& g, bool& sc) {
+        j = sj[wib][k];
         const float4 t = s4[wib][k];
         const float2 hb = sb[wib][k];
         const float dx = p[0] - t.x, dy = p[1] - t.y, dz = p[2] - t.z;
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const int gd = band_decide(r2, hi2f, tol_i);
         const int sd = band_decide(r2, hb.x, hb.y);
-        bool g = gd == 1, sc = sd == 1;
-        if (gd < 0 || sd < 0) exact_pair(j, g, sc);
-        if (!(g || sc)) continue;
+        g = gd == 1;
+        sc = sd == 1;
+        return gd < 0 || sd < 0;
+      };
+      auto emit = [&](int32_t j, bool g, bool sc) {
+        if (j == s || !(g || sc)) return;
         const uint32_t e = (uint32_t)j | (g ? kGatherBit : 0u) | (sc ? kScatterBit : 0u);
         if (kg + ks < cap_pp) {
           const int64_t kk = g ? kg : cap_pp - 1 - ks;
           ell[wbase + kk * 32] = e;
         }
         if (g) ++kg; else ++ks;
+      };
+      while (hit) {
+        const int k1 = __ffs(hit) - 1;
+        hit &= hit - 1u;
+        const bool two = hit != 0u;
+        const int k2 = two ? __ffs(hit) - 1 : k1;
+        hit &= two ? hit - 1u : hit;
+        int32_t j1, j2;
+        bool g1, s1, g2, s2;
+        const bool x1 = decide(k1, j1, g1, s1);
+        const bool x2 = decide(k2, j2, g2, s2);
+        if (x1 && j1 != s) exact_pair(j1, g1, s1);
+        if (two && x2 && j2 != s) exact_pair(j2, g2, s2);
+        emit(j1, g1, s1);
+        if (two) emit(j2, g2, s2);
       }
     };
     if (lane == 0) stk[wib][0] = (ni > 0) ? 0 : (int32_t)ni;

@@ -615,8 +615,9 @@ template <class P, int MB, int MODE>
 void launch_variant(Plan* plan, cudaStream_t st, const typename P::Args& a) {
   const size_t smem = (MODE == 1 || MODE == 3) ? Stage<P>::bytes(mode_depth<P, MODE>()) : 0;
   const void* fn = (const void*)k_sweep<P, MB, MODE>;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the default cap (48 KB, static shared memory included) is raised for
+  // every ring variant, so that a ring of exactly 48 KB launches as well
+  if (smem > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int grid = sweep_grid(plan, fn, P::BLOCK, (int)smem);
   typename P::Args b = a;
   b.c.lpt = P::LPT && lpt_worthwhile(plan->ly.nw, (int64_t)grid * P::BLOCK / 32);
