@@ -369,10 +369,13 @@ crk_status crk_cool_exact(crk_plan* plan, crk_stream_t stream, int64_t n,
  * blocks per SM (so three register caps and occupancies; variant % 3), each
  * with the neighbor records read straight from global memory when the pair is
  * evaluated (variants 0-2), copied one list entry ahead through a per-thread
- * shared-memory ring with cp.async (variants 3-5), loaded one list entry ahead
- * into a register double buffer (variants 6-8), or the same two with several
- * entries in flight (a deeper ring, variants 9-11; rotating register buffers,
- * variants 12-14: four for the light sweeps, three for the heavy ones).
+ * shared-memory ring with cp.async, each lane its own record (variants 3-5),
+ * loaded one list entry ahead into a register double buffer (variants 6-8),
+ * copied into the ring by the whole warp, consecutive lanes taking consecutive
+ * 16-byte pieces of one record (variants 9-11 densely, 15-17 in power-of-two
+ * lane groups per record), or loaded into rotating register buffers with
+ * several entries in flight (variants 12-14: four buffers for the light
+ * sweeps, three for the heavy ones).
  * This call runs crk_moments, crk_rates and, when g_dvdt and g_dudt are given,
  * crk_adjoint on the caller's data with each variant `repeats` times, times
  * every sweep with CUDA events and keeps the fastest variant per sweep in the
@@ -381,7 +384,7 @@ crk_status crk_cool_exact(crk_plan* plan, crk_stream_t stream, int64_t n,
  * choice_out (optional, host int32[8]) receives the chosen variant per sweep,
  * ms_out (optional, host float[8][CRK_TUNE_VARIANTS]) the mean milliseconds of
  * every variant.  Synchronises.  Requires a built workspace. */
-#define CRK_TUNE_VARIANTS 15
+#define CRK_TUNE_VARIANTS 18
 crk_status crk_autotune(crk_plan* plan, crk_stream_t stream, void* ws, const void* m,
                         const void* v, const void* u, const void* g_dvdt, const void* g_dudt,
                         int32_t repeats, int32_t* choice_out, float* ms_out);

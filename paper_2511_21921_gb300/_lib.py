@@ -100,7 +100,7 @@ _SIGS = {
                             _VP, _VP, _VP, _VP, C.c_double, _VP, _VP, _VP]),
 }
 CRK_STATIC_MAX_PARTICLES = 65536
-CRK_TUNE_VARIANTS = 15  # launch variants per sweep (include/crk.h)
+CRK_TUNE_VARIANTS = 18  # launch variants per sweep (include/crk.h)
 
 _lib = None
 

@@ -230,7 +230,7 @@ template <class R, bool VAR = false> struct PassA2 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 5, MB2 = 6;  // resident-block variants
-  static constexpr int DEEP = 3;  // ring slots / register buffers of the deep load modes
+  static constexpr int DEEP = 3;  // register buffers of load mode 4
   static constexpr int QUEUE = Q_A_C2;
   using Real = R;
   static constexpr int SW0 = Rec<R>::C2, SW1 = 4;  // words staged per neighbor
@@ -557,7 +557,7 @@ template <class R> struct PassA1 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 6, MB2 = 8;  // resident-block variants
-  static constexpr int DEEP = 3;  // ring slots / register buffers of the deep load modes
+  static constexpr int DEEP = 3;  // register buffers of load mode 4
   static constexpr int QUEUE = Q_A_C1;
   using Real = R;
   static constexpr int SW0 = ARec<R>::A1, SW1 = 0;  // words staged per neighbor
@@ -721,7 +721,7 @@ template <class R> struct PassAB2 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 10, MB2 = 12;  // resident-block variants
-  static constexpr int DEEP = 3;  // ring slots / register buffers of the deep load modes
+  static constexpr int DEEP = 3;  // register buffers of load mode 4
   static constexpr int QUEUE = Q_A_B2;
   using Real = R;
   static constexpr int SW0 = ARec<R>::A2, SW1 = 0;  // words staged per neighbor
@@ -869,7 +869,7 @@ template <class R> struct PassAB1 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 64;
   static constexpr int MB0 = 1, MB1 = 14, MB2 = 16;  // resident-block variants
-  static constexpr int DEEP = 4;  // ring slots / register buffers of the deep load modes
+  static constexpr int DEEP = 4;  // register buffers of load mode 4
   static constexpr int QUEUE = Q_A_B1;
   using Real = R;
   static constexpr int SW0 = ARec<R>::A3, SW1 = 0;  // words staged per neighbor

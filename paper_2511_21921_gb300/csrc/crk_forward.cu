@@ -39,7 +39,7 @@ template <class R> struct PassB1 {
   static constexpr bool GATHER = true;
   static constexpr int BLOCK = 256;
   static constexpr int MB0 = 1, MB1 = 3, MB2 = 4;  // resident-block variants
-  static constexpr int DEEP = 4;  // ring slots / register buffers of the deep load modes
+  static constexpr int DEEP = 4;  // register buffers of load mode 4
   static constexpr int QUEUE = Q_B1;
   using Real = R;
   static constexpr int SW0 = Rec<R>::B1, SW1 = 0;  // words staged per neighbor
@@ -115,7 +115,7 @@ template <class R> struct PassB2 {
   static constexpr bool GATHER = true;
   static constexpr int BLOCK = 256;
   static constexpr int MB0 = 1, MB1 = 3, MB2 = 4;  // resident-block variants
-  static constexpr int DEEP = 4;  // ring slots / register buffers of the deep load modes
+  static constexpr int DEEP = 4;  // register buffers of load mode 4
   static constexpr int QUEUE = Q_B2;
   using Real = R;
   static constexpr int SW0 = Rec<R>::B2, SW1 = 0;  // words staged per neighbor
@@ -239,7 +239,7 @@ template <class R> struct PassC1 {
   static constexpr bool GATHER = true;
   static constexpr int BLOCK = 256;
   static constexpr int MB0 = 1, MB1 = 4, MB2 = 5;  // resident-block variants
-  static constexpr int DEEP = 4;  // ring slots / register buffers of the deep load modes
+  static constexpr int DEEP = 4;  // register buffers of load mode 4
   static constexpr int QUEUE = Q_C1;
   using Real = R;
   static constexpr int SW0 = Rec<R>::C1, SW1 = 0;  // words staged per neighbor
@@ -369,7 +369,7 @@ template <class R, bool VAR = false> struct PassC2 {
   static constexpr bool GATHER = false;
   static constexpr int BLOCK = 128;
   static constexpr int MB0 = 2, MB1 = 3, MB2 = 4;  // resident-block variants
-  static constexpr int DEEP = 3;  // ring slots / register buffers of the deep load modes
+  static constexpr int DEEP = 3;  // register buffers of load mode 4
   static constexpr int QUEUE = Q_C2;
   using Real = R;
   static constexpr int SW0 = Rec<R>::C2, SW1 = 0;  // words staged per neighbor

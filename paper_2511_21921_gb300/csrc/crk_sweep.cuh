@@ -85,20 +85,32 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Staging ring of the record-ring load modes: every thread owns NS slots (two,
-// or the pass's DEEP) of SV 16-byte vectors each, laid out [slot][vector]
-// [thread] so that the threads of a warp touch consecutive 16-byte words (no
-// bank conflicts).  The neighbor records of list entries k+1 .. k+NS-1 are in
-// flight while the pair of entry k is evaluated from its slot, so the gather
-// latency overlaps the arithmetic instead of stalling it.  Each thread reads
-// back only its own slots, and every value it reads is consumed before the
-// slot is refilled.
+// Staging rings of the record-ring load modes: every thread owns two slots,
+// each holding one neighbor record of SV 16-byte vectors.  The record of list
+// entry k+1 is in flight while the pair of entry k is evaluated from its slot,
+// so the gather latency overlaps the arithmetic instead of stalling it.  Two
+// ways to fill them:
+//  * per lane (Stage, load mode 1): each lane copies its own neighbor's
+//    record, slots laid out [slot][vector][thread] so that a warp's 16-byte
+//    copies land on consecutive words.  One cp.async instruction then reads 32
+//    records' lines and costs the L1 about one shared-memory write wavefront
+//    per lane.
+//  * by the warp (WarpStage, load modes 3 and 5): consecutive lanes copy
+//    consecutive vectors of the same record, so one instruction touches the
+//    lines of a few records and writes them nearly contiguously -- densely
+//    (mode 3: the warp's 32 * SV vectors in order, SV instructions) or in
+//    power-of-two lane groups per record (mode 5: fewer index operations,
+//    some lanes idle).  Slots are laid out [slot][thread][vector] with an odd
+//    stride SP >= SV, which keeps the warp's fill and each lane's read of its
+//    own slot (8 lanes per wavefront) free of bank conflicts.  A lane's record
+//    is written by other lanes, so the warp meets (__syncwarp) after its copies
+//    land and before a slot is refilled.
 template <class P> struct Stage {
   using R = typename P::Real;
   static constexpr int V0 = P::SW0 * (int)sizeof(R) / 16;  // vectors of source 0
   static constexpr int V1 = P::SW1 * (int)sizeof(R) / 16;  // vectors of source 1
   static constexpr int SV = V0 + V1;
-  static constexpr size_t bytes(int ns) { return (size_t)ns * SV * P::BLOCK * 16; }
+  static constexpr size_t bytes = (size_t)2 * SV * P::BLOCK * 16;
   __device__ static void issue(const typename P::Args& a, float4* ring, int slot, uint32_t j) {
     const int t = threadIdx.x;
     const float4* g0 = reinterpret_cast<const float4*>(P::src0(a)) + (size_t)j * V0;
@@ -124,6 +136,66 @@ template <class P> struct Stage {
   }
 };
 
+template <class P, bool GROUPED> struct WarpStage {
+  using R = typename P::Real;
+  static constexpr int V0 = Stage<P>::V0, V1 = Stage<P>::V1, SV = Stage<P>::SV;
+  static constexpr int SP = SV | 1;
+  static_assert(SV <= 32, "record too long for the warp-filled ring");
+  // grouped: lanes per record (a power of two >= SV); one instruction copies
+  // the records of 32 / G lanes and G instructions fill the warp's 32 slots
+  static constexpr int G = SV <= 1 ? 1 : SV <= 2 ? 2 : SV <= 4 ? 4 : SV <= 8 ? 8 : SV <= 16 ? 16 : 32;
+  static constexpr int PER = 32 / G;
+  static constexpr size_t bytes = (size_t)2 * SP * P::BLOCK * 16;
+  __device__ static const float4* vec(const typename P::Args& a, uint32_t jo, int v) {
+    if (V1 == 0 || v < V0) return reinterpret_cast<const float4*>(P::src0(a)) + (size_t)jo * V0 + v;
+    return reinterpret_cast<const float4*>(P::src1(a)) + (size_t)jo * (V1 > 0 ? V1 : 1) + (v - V0);
+  }
+  // All 32 lanes call this together with a valid neighbor index each (a lane
+  // without a record passes any valid particle; its slot is not read).
+  // Dense: the warp's 32 * SV vectors in order, vector q = 32 i + lane of
+  // instruction i being vector q % SV of lane q / SV's record, every lane
+  // busy.  Grouped: lane l copies vector l % G of the record of lane
+  // i * PER + l / G, lanes with l % G >= SV idle.
+  __device__ static void issue(const typename P::Args& a, float4* ring, int slot, uint32_t j) {
+    const int lane = threadIdx.x & 31;
+    float4* base = ring + ((size_t)slot * P::BLOCK + (threadIdx.x - lane)) * SP;
+    if constexpr (GROUPED) {
+      const int h = lane / G, v = lane % G;
+      const bool act = v < SV;
+      const float4* src0 = vec(a, 0, act ? v : 0);
+      const size_t stride = (V1 == 0 || v < V0) ? V0 : (V1 > 0 ? V1 : 1);
+      float4* dst = base + h * SP + v;
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        const uint32_t jo = __shfl_sync(kFull, j, i * PER + h);
+        if (act) cp_async16(dst + i * PER * SP, src0 + (size_t)jo * stride);
+      }
+    } else {
+      constexpr int DO = 32 / SV, DV = 32 % SV;
+      int o = lane / SV, v = lane % SV;
+#pragma unroll
+      for (int i = 0; i < SV; ++i) {
+        const uint32_t jo = __shfl_sync(kFull, j, o);
+        cp_async16(base + o * SP + v, vec(a, jo, v));
+        o += DO;
+        v += DV;
+        if (v >= SV) v -= SV, ++o;
+      }
+    }
+  }
+  __device__ static void read(const float4* ring, int slot, R* r0, R* r1) {
+    const float4* me = ring + ((size_t)slot * P::BLOCK + threadIdx.x) * SP;
+    float4* o0 = reinterpret_cast<float4*>(r0);
+#pragma unroll
+    for (int v = 0; v < V0; ++v) o0[v] = me[v];
+    if constexpr (V1 > 0) {
+      float4* o1 = reinterpret_cast<float4*>(r1);
+#pragma unroll
+      for (int v = 0; v < V1; ++v) o1[v] = me[V0 + v];
+    }
+  }
+};
+
 // Neighbor record(s) of j straight from global memory (the unstaged path).
 template <class P>
 __device__ __forceinline__ void load_sources(const typename P::Args& a, uint32_t j,
@@ -145,10 +217,6 @@ constexpr int sweep_regs(int block, int minb) {
   return r > 255 ? 255 : r;
 }
 
-// Ring slots and register buffers of a load mode (see k_sweep).
-template <class P, int MODE> constexpr int mode_depth() {
-  return (MODE == 3 || MODE == 4) ? P::DEEP : 2;
-}
 
 // Persistent sweep: warps pull 32-particle work items from an atomic queue --
 // 32 consecutive sorted particles, or 32 entries of a work list (the active
@@ -156,16 +224,16 @@ template <class P, int MODE> constexpr int mode_depth() {
 // union-list length).  MINB (minimum resident blocks per SM) sets the register
 // cap and MODE how the neighbor records reach the pair arithmetic: 0 loaded
 // from global memory when the pair is evaluated, 1 copied one entry ahead
-// through the shared-memory ring, 2 loaded one entry ahead into a register
-// double buffer, 3 and 4 the same two with DEEP - 1 entries in flight (the
-// light passes, whose few flops per pair cannot cover one gather's latency).
-// Each pass is compiled for three MINB values in each mode and the autotuner
-// picks one of the fifteen per plan.
+// through the shared-memory ring, each lane its own record, 2 loaded one entry
+// ahead into a register double buffer, 3 and 5 the ring filled by the whole
+// warp (densely, in lane groups), 4 DEEP register buffers with DEEP - 1
+// entries in flight (the light passes, whose few flops per pair cannot cover
+// one gather's latency).  Each pass is compiled for three MINB values in each
+// mode and the autotuner picks one of the eighteen per plan.
 template <class P, int MINB, int MODE>
 __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MINB))
     k_sweep(const typename P::Args a) {
-  constexpr bool STG = MODE == 1 || MODE == 3;
-  constexpr int NS = mode_depth<P, MODE>();
+  constexpr bool STG = MODE == 1 || MODE == 3 || MODE == 5;
   const int lane = threadIdx.x & 31;
   int32_t* q = &a.c.hdr->queue[P::QUEUE];
   extern __shared__ float4 ring[];
@@ -209,7 +277,7 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
       auto safe = [&](uint32_t e) -> uint32_t {
         return index_ok(a.c.hdr, e & kIdxMask, a.c.n) ? e : (uint32_t)s;
       };
-      if constexpr (NS == 2) {
+      if constexpr (MODE == 1) {
         uint32_t e_next = tot > 0 ? safe(entry(0)) : 0u;
         if (tot > 0) Stage<P>::issue(a, ring, 0, e_next & kIdxMask);
         cp_async_commit();
@@ -228,41 +296,41 @@ __global__ void __launch_bounds__(P::BLOCK) __maxnreg__(sweep_regs(P::BLOCK, MIN
           }
         }
       } else {
-        // NS slots: entry k lives in slot k % NS and its copy is commit group
-        // k; the loop is unrolled by NS so that slots and entries are static.
-        uint32_t ent[NS];
-#pragma unroll
-        for (int i = 0; i < NS - 1; ++i) {
-          ent[i] = i < tot ? safe(entry(i)) : 0u;
-          if (i < tot) Stage<P>::issue(a, ring, i, ent[i] & kIdxMask);
+        // The warp's copies of step k are commit group k.  Each step waits
+        // for the lane's own copies of entry k and meets the warp: then every
+        // copy into slot k & 1 is visible and every lane has finished reading
+        // the other slot, which takes entry k+1.
+        using WS = WarpStage<P, MODE == 5>;
+        // a lane without a record this step copies its own (or particle 0's)
+        const uint32_t own = live ? (uint32_t)s : 0u;
+        auto idx = [&](int k, uint32_t e) -> uint32_t { return k < tot ? e & kIdxMask : own; };
+        uint32_t e_cur = tot > 0 ? safe(entry(0)) : 0u;
+        WS::issue(a, ring, 0, idx(0, e_cur));
+        cp_async_commit();
+        uint32_t e_next = tot > 1 ? safe(entry(1)) : 0u;
+        for (int k = 0; k < wmax; ++k) {
+          cp_async_wait<0>();
+          __syncwarp();
+          WS::issue(a, ring, (k + 1) & 1, idx(k + 1, e_next));
           cp_async_commit();
-        }
-        uint32_t e_ahead = NS - 1 < tot ? safe(entry(NS - 1)) : 0u;
-        for (int k0 = 0; k0 < wmax; k0 += NS) {
-#pragma unroll
-          for (int d = 0; d < NS; ++d) {
-            const int k = k0 + d;
-            const int sl = (d + NS - 1) % NS;  // the slot of entry k + NS - 1
-            ent[sl] = e_ahead;
-            if (k + NS - 1 < tot) Stage<P>::issue(a, ring, sl, e_ahead & kIdxMask);
-            cp_async_commit();
-            e_ahead = k + NS < tot ? safe(entry(k + NS)) : 0u;
-            cp_async_wait<NS - 1>();  // groups 0 .. k have landed
-            if (k < tot) {
-              Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
-              Stage<P>::read(ring, d, r0, r1);
-              P::pair_s(a, st, r0, r1, ent[d] & kIdxMask, ent[d]);
-            }
+          const uint32_t e = e_cur;
+          e_cur = e_next;
+          e_next = k + 2 < tot ? safe(entry(k + 2)) : 0u;
+          if (k < tot) {
+            Real r0[P::SW0], r1[P::SW1 > 0 ? P::SW1 : 1];
+            WS::read(ring, k & 1, r0, r1);
+            P::pair_s(a, st, r0, r1, e & kIdxMask, e);
           }
         }
       }
       cp_async_wait<0>();
+      __syncwarp();  // no copy into the warp's slots is in flight past the item
     } else if constexpr (MODE == 4) {
       // DEEP register buffers: the records of entries k+1 .. k+DEEP-1 are in
       // flight while the pair of entry k is evaluated, and each list entry is
       // read DEEP steps before its record.  Unrolled by DEEP so that the
       // buffers rotate without register copies.
-      constexpr int D = NS;
+      constexpr int D = P::DEEP;
       const int tot = lg + ls;
       const int wmax = P::GATHER && !its ? a.c.wlen_g[wi] : __reduce_max_sync(kFull, tot);
       auto raw = [&](int k) -> uint32_t {
@@ -613,7 +681,8 @@ template <class R> struct PairC2 {
 
 template <class P, int MB, int MODE>
 void launch_variant(Plan* plan, cudaStream_t st, const typename P::Args& a) {
-  const size_t smem = (MODE == 1 || MODE == 3) ? Stage<P>::bytes(mode_depth<P, MODE>()) : 0;
+  const size_t smem = MODE == 1 ? Stage<P>::bytes
+                                : (MODE == 3 || MODE == 5 ? WarpStage<P, false>::bytes : 0);
   const void* fn = (const void*)k_sweep<P, MB, MODE>;
   // the default cap (48 KB, static shared memory included) is raised for
   // every ring variant, so that a ring of exactly 48 KB launches as well
@@ -634,7 +703,8 @@ void launch_sweep_plain(Plan* plan, cudaStream_t st, const typename P::Args& a, 
 
 // Variant v of a sweep: v % 3 picks the resident-block count (MB0..MB2),
 // v / 3 the mode (0 plain loads, 1 shared-memory ring, 2 register double
-// buffer, 3 deep ring, 4 deep register buffers).
+// buffer, 3 warp-filled ring, 4 deep register buffers, 5 warp-filled ring in
+// lane groups).
 template <class P>
 void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const char* name) {
   const int v = plan->variant[P::QUEUE];
@@ -654,6 +724,9 @@ void launch_sweep(Plan* plan, cudaStream_t st, const typename P::Args& a, const 
     case 12: launch_variant<P, P::MB0, 4>(plan, st, a); break;
     case 13: launch_variant<P, P::MB1, 4>(plan, st, a); break;
     case 14: launch_variant<P, P::MB2, 4>(plan, st, a); break;
+    case 15: launch_variant<P, P::MB0, 5>(plan, st, a); break;
+    case 16: launch_variant<P, P::MB1, 5>(plan, st, a); break;
+    case 17: launch_variant<P, P::MB2, 5>(plan, st, a); break;
     default: launch_variant<P, P::MB0, 0>(plan, st, a); break;
   }
 }

@@ -1,7 +1,8 @@
 """Every compiled launch variant of the eight neighbor sweeps -- three register
-caps times five ways of bringing the neighbor records to the pair arithmetic
-(plain loads, shared-memory ring, register double buffer, and the ring and the
-register buffers with several records in flight) -- gives the oracle's
+caps times six ways of bringing the neighbor records to the pair arithmetic
+(plain loads, a shared-memory ring filled per lane or by the whole warp in two
+layouts, a register double buffer, rotating register buffers with several
+records in flight) -- gives the oracle's
 results: the forward fields and rates element by element, the adjoint through
 a dot test against the oracle's forward-mode derivative, and the active-set
 path, whose sweeps walk a compacted work list instead of consecutive warps."""
