@@ -5,7 +5,7 @@ The computation lives in ``libcrk`` (CUDA C++ for sm_103a, C ABI in
 :mod:`.solver` a torch-tensor wrapper with an autograd function.
 :mod:`.synth` generates the seeded synthetic workloads.
 """
-__all__ = ["Solver", "CRKRates", "rates", "make_params"]
+__all__ = ["Solver", "CRKRates", "rates", "make_params", "copy_"]
 
 
 def __getattr__(name):

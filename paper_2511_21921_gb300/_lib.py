@@ -68,6 +68,7 @@ _SIGS = {
     "crk_neighbors_csr": (C.c_int, [_VP, _VP, _VP, C.c_int32, _VP, _VP, C.c_int64,
                                     C.POINTER(C.c_int64)]),
     "crk_stats_get": (C.c_int, [_VP, _VP, _VP, C.POINTER(crk_stats)]),
+    "crk_copy": (C.c_int, [_VP, _VP, _VP, C.c_size_t]),
     "crk_status_poll": (C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_int)]),
     "crk_status_string": (C.c_char_p, [C.c_int]),
     "crk_timing_enable": (C.c_int, [_VP, C.c_int32]),
@@ -203,6 +204,10 @@ def crk_stats_get(plan, stream, ws) -> crk_stats:
     s = crk_stats()
     check(load().crk_stats_get(_VP(plan), _VP(stream), _VP(ws), C.byref(s)), "crk_stats_get")
     return s
+
+
+def crk_copy(stream, dst, src, nbytes) -> None:
+    check(load().crk_copy(_VP(stream), _VP(dst), _VP(src), int(nbytes)), "crk_copy")
 
 
 def crk_status_poll(plan, stream, ws) -> int:

@@ -37,6 +37,18 @@ def _stream():
     return torch.cuda.current_stream().cuda_stream
 
 
+def copy_(dst: torch.Tensor, src: torch.Tensor) -> torch.Tensor:
+    """``dst.copy_(src)`` for contiguous tensors of one dtype and shape through
+    ``crk_copy`` (the SMs move the bytes) on the current stream: the staging
+    copy between page-locked host memory and the device each step."""
+    if dst.dtype != src.dtype or dst.shape != src.shape:
+        raise ValueError("copy_: dtype and shape must match")
+    if not (dst.is_contiguous() and src.is_contiguous()):
+        raise ValueError("copy_: tensors must be contiguous")
+    L.crk_copy(_stream(), dst.data_ptr(), src.data_ptr(), src.numel() * src.element_size())
+    return dst
+
+
 class Solver:
     """Plan + workspace for up to ``n_max`` particles in ``n_boxes_max`` boxes."""
 

@@ -41,3 +41,13 @@ def test_argument_errors_are_synchronous():
     assert lib.crk_workspace_size(None, 10, 1, C.byref(b)) == L.CRK_EINVAL
     assert lib.crk_moments(None, None, None, None, None, None) == L.CRK_EINVAL
     assert lib.crk_rates(None, None, None, None, None, None, None, None, None) == L.CRK_EINVAL
+
+
+def test_copy_argument_errors():
+    """crk_copy rejects bad arguments before any CUDA call; zero bytes is a no-op."""
+    lib = L.load()
+    assert lib.crk_copy(None, None, None, 0) == L.CRK_OK
+    assert lib.crk_copy(None, None, C.c_void_p(0x1000), 16) == L.CRK_EINVAL
+    assert lib.crk_copy(None, C.c_void_p(0x1000), None, 16) == L.CRK_EINVAL
+    # overlapping ranges
+    assert lib.crk_copy(None, C.c_void_p(0x1008), C.c_void_p(0x1000), 16) == L.CRK_EINVAL
