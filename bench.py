@@ -116,9 +116,14 @@ def profiled_traffic(kernel: str, workload: str):
 
 def profiled_limiter(kernel: str, workload: str):
     """The busiest on-chip unit of ``kernel`` in its committed ncu summary (same
-    build digest): L1 throughput, issue activity and FMA-pipe activity, in %."""
-    p = _profile_of(kernel, workload)
-    if p and "L1 throughput, %" not in p[2]:
+    build digest): L1 throughput, issue activity and FMA-pipe activity, in %.
+    A full-size workload is captured for DRAM bytes only (one pass), so its
+    on-chip figures come from the same kernel's full capture on the small box."""
+    p = None
+    for wl in (workload, SMALL_WORKLOAD):
+        p = _profile_of(kernel, wl)
+        if p and "L1 throughput, %" in p[2]:
+            break
         p = None
     if not p:
         return None
@@ -131,7 +136,7 @@ def profiled_limiter(kernel: str, workload: str):
         except (IndexError, ValueError):
             return None
     return {"l1_throughput_pct": pct("L1 throughput, %"), "issue_active_pct": pct("issue active, %"),
-            "fma_pipe_pct": pct("FMA pipe active, %"),
+            "fma_pipe_pct": pct("FMA pipe active, %"), "workload": p[1].get("workload"),
             "source": os.path.relpath(path, ROOT)}
 
 
