@@ -58,13 +58,17 @@ __global__ void k_keys(const double* __restrict__ x, const R* __restrict__ h,
   double L = box_L[b];
   uint32_t q[3];
   bool ok = true;
+  // cells per unit length: one FP64 division per particle instead of one per
+  // coordinate (GB300 runs FP64 at about 1/64 of the FP32 rate); exact for a
+  // power-of-two box side
+  const double cells = (double)(1u << bits);
+  const double scale = cells / L;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     double xa = x[a * n + i];
     if (!isfinite(xa)) { set_status(hdr, CRK_ENONFINITE); ok = false; }
     else if (!(xa >= 0.0 && xa < L)) { set_status(hdr, CRK_EDOMAIN); ok = false; }
-    const double cells = (double)(1u << bits);
-    double t = ok ? floor(xa / L * cells) : 0.0;
+    double t = ok ? floor(xa * scale) : 0.0;
     t = t < 0.0 ? 0.0 : (t > cells - 1.0 ? cells - 1.0 : t);
     q[a] = (uint32_t)t;
   }
@@ -302,24 +306,48 @@ __global__ void k_bucket(const R* __restrict__ xs, const R* __restrict__ hs,
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbk) return;
   int64_t s0 = b * kBucket, s1 = min(n, s0 + kBucket);
-  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-  double hm = 0.0;
-  for (int64_t s = s0; s < s1; ++s) {
+  int64_t node = ni + b;
+  if constexpr (sizeof(R) == 4) {
+    // mixed form: bounds of the float high parts, each widened by one float
+    // step, contain the double-float positions (a high part is the position
+    // rounded to nearest, so the position lies within half a step of it);
+    // no FP64 arithmetic (GB300 runs FP64 at about 1/64 of the FP32 rate)
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float hm = 0.f;
+    for (int64_t s = s0; s < s1; ++s) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float p = (float)xs[a * n + s];
+        lo[a] = fminf(lo[a], p);
+        hi[a] = fmaxf(hi[a], p);
+      }
+      hm = fmaxf(hm, (float)hs[s]);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double p = xpos(xs, n, s, a);
-      lo[a] = fmin(lo[a], p);
-      hi[a] = fmax(hi[a], p);
+      aabb[a * nt + node] = nextafterf(lo[a], -INFINITY);
+      aabb[(3 + a) * nt + node] = nextafterf(hi[a], INFINITY);
     }
-    hm = fmax(hm, (double)hs[s]);
-  }
-  int64_t node = ni + b;
+    hmaxn[node] = hm;
+  } else {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    double hm = 0.0;
+    for (int64_t s = s0; s < s1; ++s) {
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    aabb[a * nt + node] = __double2float_rd(lo[a]);
-    aabb[(3 + a) * nt + node] = __double2float_ru(hi[a]);
+      for (int a = 0; a < 3; ++a) {
+        double p = xpos(xs, n, s, a);
+        lo[a] = fmin(lo[a], p);
+        hi[a] = fmax(hi[a], p);
+      }
+      hm = fmax(hm, (double)hs[s]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      aabb[a * nt + node] = __double2float_rd(lo[a]);
+      aabb[(3 + a) * nt + node] = __double2float_ru(hi[a]);
+    }
+    hmaxn[node] = __double2float_ru(hm);
   }
-  hmaxn[node] = __double2float_ru(hm);
   brange[node] = boxid[s0];
   brange[nt + node] = boxid[s1 - 1];
 }
@@ -949,20 +977,37 @@ __global__ void __launch_bounds__(kBalance)
     const int64_t q = s >> 5;
     if ((t & 31) == 0 && q * 32 < n) seq_cost[q] = (q * 32 + 32 <= n) ? um : -1;
   }
-  __syncthreads();
   if (blockIdx.x == 0 && t == 0) hdr->n_all = (int32_t)n;
-  if (!live) return;
-  int ru = 0;
-  for (int k = 0; k < m; ++k) {
-    const int uk = lu[k];
-    ru += (uk > u || (uk == u && k < t)) ? 1 : 0;
+  // bitonic sort of (length + 1, 255 - index) in decreasing order: longest
+  // first, ties by index; the slots past the run's end sort last
+  uint32_t* key = reinterpret_cast<uint32_t*>(lu);
+  key[t] = ((uint32_t)(u + 1) << 8) | (uint32_t)(kBalance - 1 - t);
+  __syncthreads();
+#pragma unroll
+  for (int k = 2; k <= kBalance; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int tx = t ^ j;
+      if (tx > t) {
+        const uint32_t a = key[t], b = key[tx];
+        if ((a < b) == ((t & k) == 0)) {
+          key[t] = b;
+          key[tx] = a;
+        }
+      }
+      __syncthreads();
+    }
   }
-  items_u[base + ru] = (int32_t)s;
+  // slot r now holds the particle of rank r
+  if (t >= m) return;
+  const uint32_t kr = key[t];
+  const int ur = (int)(kr >> 8) - 1;
+  items_u[base + t] = (int32_t)(base + (kBalance - 1 - (int)(kr & 255u)));
   // the first (longest) particle of each 32-particle item gives the item's
   // cost; a partial item (the last one) gets -1
-  if ((ru & 31) == 0) {
-    const int64_t q = (base + ru) >> 5;
-    cost[q] = (base + ru + 32 <= n) ? u : -1;
+  if ((t & 31) == 0) {
+    const int64_t q = (base + t) >> 5;
+    cost[q] = (base + t + 32 <= n) ? ur : -1;
   }
 }
 
