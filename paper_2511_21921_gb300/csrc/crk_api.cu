@@ -40,6 +40,7 @@ Layout make_layout(const crk_params& p, int64_t n, int32_t nb) {
   };
   L.hdr = take(sizeof(DevHeader));
   L.box_L = take(8 * (size_t)std::max(nb, 1));
+  L.hbox = take(4 * (size_t)std::max(nb, 1));
   L.key0 = take(8 * N);
   L.key1 = take(8 * N);
   L.val0 = take(4 * N);

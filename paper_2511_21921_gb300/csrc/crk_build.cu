@@ -47,13 +47,40 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
   return r;
 }
 
+// Morton keys in caller order; also the largest smoothing length of each box
+// (hbox, float bits, zeroed by the caller): one atomic per block and box
+// segment, since a block's consecutive particles lie in one box or a few.
 template <class R>
-__global__ void k_keys(const double* __restrict__ x, const R* __restrict__ h,
+__global__ void __launch_bounds__(256) k_keys(const double* __restrict__ x, const R* __restrict__ h,
                        const int64_t* __restrict__ box_off, const double* __restrict__ box_L,
                        int32_t nb, int64_t n, int bits, uint64_t* __restrict__ keys,
-                       int32_t* __restrict__ vals, DevHeader* hdr) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+                       int32_t* __restrict__ vals, unsigned int* __restrict__ hbox,
+                       DevHeader* hdr) {
+  __shared__ float wmax[8];
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x;
+  int64_t i = i0 + threadIdx.x;
+  const bool live = i < n;
+  const int64_t ilast = min(i0 + (int64_t)blockDim.x, n) - 1;
+  const int bfirst = box_of(box_off, nb, i0), blast = box_of(box_off, nb, ilast);
+  float hmx = 0.f;
+  if (live) {
+    const double hv = (double)h[i];
+    if (isfinite(hv) && hv > 0.0) hmx = __double2float_ru(hv);
+  }
+  if (bfirst == blast) {
+    float m = hmx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+      atomicMax(hbox + bfirst, __float_as_uint(m));
+    }
+  } else if (live) {
+    atomicMax(hbox + box_of(box_off, nb, i), __float_as_uint(hmx));
+  }
+  if (!live) return;
   int b = box_of(box_off, nb, i);
   double L = box_L[b];
   uint32_t q[3];
@@ -549,7 +576,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
     const double* __restrict__ box_L, int64_t n, int64_t nbk, int64_t ni, int64_t nt,
     const float* __restrict__ nrec, const float4* __restrict__ p4, int32_t* __restrict__ cnt_g, int32_t* __restrict__ cnt_s, int32_t* __restrict__ wlen_g,
     int32_t* __restrict__ wlen_s, uint32_t* __restrict__ ell, int64_t cap_pp, DevHeader* hdr,
-    const double* __restrict__ xd, const int32_t* __restrict__ perm) {
+    const double* __restrict__ xd, const int32_t* __restrict__ perm,
+    const float* __restrict__ hbox) {
   constexpr int XW = Prec<R>::XW;
   constexpr bool MIXED = sizeof(R) == 4;
   __shared__ int32_t stk[kNbrWarps][kNodeStack];
@@ -617,7 +645,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) k_nbr(
     group_bounds(act, p, (float)hi, gc, ge, hg);
     // nearest-image staging is exact for every pair in reach when the group
     // extent plus the largest search radius stays below half the box
-    const float reach = fmaxf(hg, __ldg(nrec + 6));  // h_max of the root
+    const float reach = fmaxf(hg, __ldg(hbox + b));  // the largest h of the box
     const bool fast = sizeof(R) == 4 &&
                       2.f * fmaxf(ge[0], fmaxf(ge[1], ge[2])) + reach < 0.49f * Lf;
     if (__popc(m) > 2 && ntodo <= 6) {
@@ -1097,7 +1125,9 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   for (int b = 48; b < 48 + box_bits; b += 8) shifts[passes++] = b;
   Phase ph_sort(plan, st, "build.keys_sort",
                 1 + passes * (2 + scan_launches((int64_t)256 * Ly.ntiles)));
-  k_keys<R><<<g256, 256, 0, st>>>(x, h, box_off, box_L, nb, n, bits, k0, v0, hdr);
+  unsigned int* hbox = reinterpret_cast<unsigned int*>(ws + Ly.hbox);
+  cudaMemsetAsync(hbox, 0, sizeof(unsigned int) * (size_t)std::max<int32_t>(nb, 1), st);
+  k_keys<R><<<g256, 256, 0, st>>>(x, h, box_off, box_L, nb, n, bits, k0, v0, hbox, hdr);
   // radix sort over the used key bits
   uint32_t* hist = reinterpret_cast<uint32_t*>(ws + Ly.hist);
   int ntiles = (int)Ly.ntiles;
@@ -1148,7 +1178,7 @@ crk_status cell_build_impl(Plan* plan, cudaStream_t st, char* ws, int64_t n, int
   const unsigned gw = (unsigned)((Ly.nw + kNbrWarps - 1) / kNbrWarps);
   k_nbr<R><<<gw, kNbrWarps * 32, 0, st>>>(k0, xs, hs, boxid, wbox, n, nbk, ni, nt, nrec, p4,
                                           cnt_g, cnt_s, wlen_g, wlen_s, ell, Ly.cap_pp, hdr, x,
-                                          perm);
+                                          perm, reinterpret_cast<const float*>(hbox));
   int32_t* cost = reinterpret_cast<int32_t*>(ws + Ly.item_cost);
   int32_t* seq_cost = reinterpret_cast<int32_t*>(ws + Ly.seq_cost);
   k_balance<<<(unsigned)((n + kBalance - 1) / kBalance), kBalance, 0, st>>>(

@@ -279,7 +279,7 @@ struct Layout {
   int64_t n = 0, nb = 0, nw = 0, nbk = 0, ni = 0, nt = 0, ntiles = 0, cap = 0, cap_pp = 0;
   int prec = 1;
   size_t total = 0;
-  size_t hdr = 0, box_L = 0;
+  size_t hdr = 0, box_L = 0, hbox = 0;
   size_t key0 = 0, key1 = 0, val0 = 0, val1 = 0, hist = 0, scan_tmp = 0;
   size_t perm = 0, boxid = 0, xs = 0, hs = 0, ms = 0, us = 0, vs = 0;
   size_t aabb = 0, hmaxn = 0, brange = 0, child = 0, parent = 0, visit = 0;
