@@ -929,6 +929,24 @@ def cpu_baseline(args, min_seconds=10.0, max_passes=20, side=0.3):
             "seconds": round(t, 3)}
 
 
+def reference_config(args):
+    """The workload the reference arm samples, described as the GPU arm describes
+    it: its whole-box pair counts are the oracle's (tests/golden/workload_pairs.json,
+    written by the committed script beside it from oracle.count_pairs)."""
+    cfg = {"workload": WORKLOAD_DESCS.get(args.workload, args.workload), "name": args.workload}
+    path = os.path.join(ROOT, "tests", "golden", "workload_pairs.json")
+    try:
+        with open(path) as fh:
+            w = json.load(fh)[args.workload]
+    except (OSError, KeyError, ValueError):
+        return cfg
+    c = w["mixed" if args.precision == "mixed" else "fp64"]
+    cfg.update({"n": w["n"], "boxes": w["boxes"], "gather_pairs": c["gather_pairs"],
+                "union_pairs": c["union_pairs"],
+                "step": "build+moments+rates" + ("" if args.fwd_only else "+adjoint")})
+    return cfg
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed step by step on the host cores,
     each step one oracle pass over a bounded sample of the workload."""
@@ -949,10 +967,10 @@ def run_reference(args):
         "higher_is_better": True, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(mean * 1e3, 3), "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESCS.get(args.workload, args.workload),
-                   "name": args.workload, "sample": sample, "gather_pairs_per_step": pairs},
+        "config": reference_config(args),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample + "; forward values plus one JVP per step"},
+                         "sample": sample + "; forward values plus one JVP per step",
+                         "sample_gather_pairs_per_step": pairs},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 

@@ -6,7 +6,7 @@ never does.  See ``crk_oracle.cpp`` for what is computed and where in the paper
 each step comes from.
 """
 from .oracle import (  # noqa: F401
-    OracleParams, build, count_ops, default_params, forward, forward_species, forward_state, jvp, neighbors, kernel, num_threads,
+    OracleParams, build, count_ops, count_pairs, default_params, forward, forward_species, forward_state, jvp, neighbors, kernel, num_threads,
     PARITY_UNPINNED,
 )
 from . import integrate  # noqa: F401,E402

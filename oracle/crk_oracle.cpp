@@ -1012,6 +1012,33 @@ int oracle_neighbors(int32_t mode, int32_t method, int64_t n, const double* x, c
   return OK;
 }
 
+// Pair counts of the whole box without storing the sets: the ordered gather
+// pairs (j in G(i), j != i) and union pairs (j in U(i)), each particle's union
+// set found by the k-d tree and every member tested with the gather
+// predicate, so the counts equal the sizes of oracle_neighbors' sets.
+int oracle_count_pairs(int64_t n, const double* x, const double* h, double L, int64_t* gather,
+                       int64_t* union_) {
+  int rc = check_inputs(n, x, h, nullptr, nullptr, nullptr, L);
+  if (rc) return rc;
+  Box box{n, x, h, L};
+  KDTree tree(&box);
+  int64_t g = 0, u = 0;
+#pragma omp parallel reduction(+ : g, u)
+  {
+    std::vector<int64_t> row;
+#pragma omp for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; ++i) {
+      row.clear();
+      tree.query(i, true, [&box](int64_t a, int64_t c) { return box.in_union(a, c); }, row);
+      u += (int64_t)row.size();
+      for (int64_t j : row) g += box.in_gather(i, j) ? 1 : 0;
+    }
+  }
+  *gather = g;
+  *union_ = u;
+  return OK;
+}
+
 // Forward evaluation.  targets == NULL evaluates every particle (OpenMP over
 // particles); otherwise only the listed particles, computing the needed
 // neighbor closure lazily on one thread.  stages: 1 volume, 2 + coefficients,

@@ -104,6 +104,9 @@ def _load():
                                              C.c_double, dp, dp, C.c_int64, dp]
             lib.oracle_kernel.restype = None
             lib.oracle_kernel.argtypes = [C.c_int64, dp, C.c_double, dp, dp, dp]
+            lib.oracle_count_pairs.restype = C.c_int
+            lib.oracle_count_pairs.argtypes = [C.c_int64, dp, dp, C.c_double,
+                                               C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
             lib.oracle_count_ops.restype = C.c_int
             lib.oracle_count_ops.argtypes = [C.c_int64, dp, dp, dp, dp, dp, C.c_double,
                                              C.POINTER(OracleParams), dp, dp, dp, dp, C.c_int32,
@@ -312,6 +315,20 @@ def neighbors(x, h, L=1.0, mode="gather", method="tree"):
         cap = int(nnz[0])
         col = np.zeros(max(cap, 1), dtype=np.int32)
     raise RuntimeError("oracle_neighbors: capacity retry failed")
+
+
+def count_pairs(x, h, L=1.0):
+    """(ordered gather pairs, ordered union pairs) of the whole box, self
+    excluded, without storing the sets (the sizes of ``neighbors``' sets)."""
+    lib = _load()
+    n = int(np.asarray(h).shape[0])
+    x = _f64(x, (3, n))
+    h = _f64(h, (n,))
+    g, u = C.c_int64(), C.c_int64()
+    rc = lib.oracle_count_pairs(n, _ptr(x), _ptr(h), float(L), C.byref(g), C.byref(u))
+    if rc != 0:
+        raise ValueError(f"oracle_count_pairs: {STATUS.get(rc, rc)}")
+    return int(g.value), int(u.value)
 
 
 def kernel(r, h):

@@ -7,8 +7,14 @@ the oracle computes one by one (its lazy target mode):
 * lognormal256: the largest configuration, 16.8 M particles in one box.
 
 All in the mixed form the benchmark runs (float pairs, double-float
-separations).  These generate a few million particles and take minutes.
+separations).  These generate a few million particles and take minutes.  The
+whole box's pair counts (ordered gather and union pairs of the lists) must
+equal the oracle's exactly (tests/golden/workload_pairs.json, written by
+make_workload_pairs.py beside it from the oracle's count_pairs).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -19,6 +25,15 @@ from paper_2511_21921_gb300 import synth
 from gpu_util import TOL, compare, run_forward, to_dev
 
 pytestmark = pytest.mark.gpu
+
+
+def _golden_counts(s, name):
+    """The list build's whole-box pair counts against the oracle's."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "workload_pairs.json")
+    with open(path) as fh:
+        want = json.load(fh)[name]["mixed"]
+    st = s.stats()
+    assert (st["gather_pairs"], st["union_pairs"]) == (want["gather_pairs"], want["union_pairs"])
 
 
 def _stratified(h, k, rng):
@@ -34,6 +49,7 @@ def test_clumpy128_sampled_parity_mixed():
     assert d["h"].max() / d["h"].min() > 50
     gpu, s = run_forward(d, "mixed")
     assert gpu["status"] == 0
+    _golden_counts(s, "clumpy128")
     tg = _stratified(d["h"], 96, np.random.default_rng(5))
     ora = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], 1.0, targets=tg)
     err = compare(gpu, ora, idx=tg)
@@ -73,6 +89,7 @@ def test_multibox64_sampled_parity_mixed():
     d = synth.load("multibox64")
     gpu, s = run_forward(d, "mixed")
     assert gpu["status"] == 0
+    _golden_counts(s, "multibox64")
     off = d["box_off"]
     nb = len(off) - 1
     sizes = np.diff(off)
@@ -98,6 +115,7 @@ def test_lognormal256_sampled_parity_mixed():
     assert n == 256 ** 3
     gpu, s = run_forward(d, "mixed")
     assert gpu["status"] == 0
+    _golden_counts(s, "lognormal256")
     tg = _stratified(d["h"], 48, np.random.default_rng(9))
     ora = oracle.forward(d["x"], d["h"], d["m"], d["v"], d["u"], 1.0, targets=tg)
     err = compare(gpu, ora, idx=tg)
